@@ -1,0 +1,361 @@
+#!/usr/bin/env python3
+"""Benchmark: Gray-code Ryser subsets/s for perm(A) mod 3 on one GB300.
+
+Workload (one "step"): the permanent of the seeded uniform 36 x 36 matrix and
+of the seeded uniform 40 x 40 matrix, each a full walk of all 2^n Gray
+indices in its own launch (one matrix per launch).  value = subsets/s
+(2^36 + 2^40 per step) with the matrices resident in HBM; e2e = the same
+through the host-pointer C entry point perm_f3 (input copied in, result
+copied out, every call).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--no-batch] [--no-cpu-baseline]
+
+With N > 1 (torchrun, one rank per GPU) every rank walks its 1/N share of each
+matrix's Gray range (Sec. 3.1's block split) and the two 64-bit counts are
+summed across ranks at the end of each step (strong scaling).
+
+--impl reference times the CPU oracle (the plain integer Ryser walk) on the
+host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "F3 Ryser Gray-code subsets/sec on 1 GB300; batched perms/sec; p50/p99 latency"
+UNIT = "subsets/s"
+SIZES = (36, 40)
+G_LOG2 = 4  # probe group of the walk: 2^G Gray indices per carried base state
+
+
+def i_alg(W: int, G: int = G_LOG2) -> float:
+    """ALU-pipe instructions per subset issued by the grouped walk: per group of
+    2^G indices, one full row step on the base (3 LOP3 per word), 2^G - 1
+    probes on the low mag word (2 LOP3 each) and 2^G zero tests (one compare)."""
+    return (3 * W + 2 * ((1 << G) - 1) + (1 << G)) / (1 << G)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def matrices():
+    from paper_2407_20205_gb300 import inputs
+    seeds = {36: inputs.SEED_N36, 40: inputs.SEED_N40}
+    return {n: inputs.uniform_matrix(seeds[n], n) for n in SIZES}
+
+
+def rank_range(n, rank, world):
+    total = 1 << n
+    q, r = divmod(total, world)
+    a = rank * q + min(rank, r)
+    ln = q + (1 if rank < r else 0)
+    return a, a + ln - 1
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(prefix="pf3_clocks_", suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        out.update({"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                    "reasons": sorted(reasons), "samples": len(rows)})
+        return out
+
+
+def cpu_sample(A, seconds_target=12.0, max_log2=34):
+    """Time the oracle's Gray walk on a bounded sub-range of A's index space,
+    on all host cores; grow the range until it takes ~seconds_target."""
+    import oracle
+    At = np.ascontiguousarray(A.T)
+    threads = oracle.max_threads()
+    lg = 22
+    while True:
+        cnt = 1 << lg
+        t0 = time.perf_counter()
+        oracle.ryser_range_par(At, 0, cnt - 1, nparts=threads * 4, nthreads=threads)
+        dt = time.perf_counter() - t0
+        if dt >= seconds_target / 4 or lg >= max_log2:
+            if dt < seconds_target and lg < max_log2:
+                # one final run sized for the target
+                lg2 = min(max_log2, lg + max(0, int(np.log2(seconds_target / max(dt, 1e-3)))))
+                if lg2 > lg:
+                    lg = lg2
+                    cnt = 1 << lg
+                    t0 = time.perf_counter()
+                    oracle.ryser_range_par(At, 0, cnt - 1, nparts=threads * 4, nthreads=threads)
+                    dt = time.perf_counter() - t0
+            return {"value": cnt / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+                    "sample": f"Gray indices 0..2^{lg}-1 of the seeded {A.shape[0]}x{A.shape[0]} matrix "
+                              f"({cnt} subsets, {dt:.2f} s wall on {threads} threads)"}
+        lg += 2
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if world > 1 and rank != 0:
+        return 0
+    mats = matrices()
+    A = mats[36]
+    info = cpu_sample(A, seconds_target=6.0)
+    per_step = int(info["sample"].split("(")[1].split(" ")[0])
+    import oracle
+    At = np.ascontiguousarray(A.T)
+    th = oracle.max_threads()
+    for _ in range(args.warmup):
+        oracle.ryser_range_par(At, 0, (1 << 20) - 1, nparts=th * 4, nthreads=th)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.ryser_range_par(At, 0, per_step - 1, nparts=th * 4, nthreads=th)
+    dt = time.perf_counter() - t0
+    value = per_step * args.steps / dt
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "perm mod 3 of seeded uniform 36x36 and 40x40 matrices over F3, "
+                                   "one matrix per launch (oracle: bounded sub-range of the 36x36 walk)",
+                       "l2": "not applicable (CPU)"},
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": th, "kind": "oracle",
+                             "sample": f"{per_step} Gray indices of the 36x36 matrix per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        print(json.dumps({"error": "no CUDA device"}))
+        return 1
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2407_20205_gb300 import binding as pf3
+
+    mats = matrices()
+    dev = torch.device("cuda", local)
+    dA = {n: torch.from_numpy(mats[n]).to(dev) for n in SIZES}
+    out = {n: torch.zeros(3, dtype=torch.int64, device=dev) for n in SIZES}
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    ranges = {n: rank_range(n, rank, world) for n in SIZES}
+
+    def step():
+        for n in SIZES:
+            a, b = ranges[n]
+            pf3.perm_f3_range_counts_async(dA[n], n, a, b, out[n], stream)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    stream.synchronize()
+
+    # timed region: K steps, each bracketed by events on the launching stream;
+    # the L2 flush runs between steps, outside the events
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(SIZES) + 1)] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    time.sleep(0.3)
+    t_wall0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            ev[k][0].record(stream)
+            for j, n in enumerate(SIZES):
+                a, b = ranges[n]
+                pf3.perm_f3_range_counts_async(dA[n], n, a, b, out[n], stream)
+                ev[k][j + 1].record(stream)
+    stream.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    barrier()
+    clk = clocks.stop()
+    step_ms = [ev[k][0].elapsed_time(ev[k][-1]) for k in range(args.steps)]
+    launch_ms = {n: [ev[k][j].elapsed_time(ev[k][j + 1]) for k in range(args.steps)] for j, n in enumerate(SIZES)}
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    # results: sum the per-rank counts (the one exchange of the range split)
+    counts = {n: out[n][:2].clone() for n in SIZES}
+    if world > 1:
+        for n in SIZES:
+            torch.distributed.all_reduce(counts[n])
+    results = {}
+    for n in SIZES:
+        p, m = [int(x) for x in counts[n].cpu()]
+        d = (p - m) * (-1 if n & 1 else 1)
+        results[n] = d % 3
+    subsets_step = sum(1 << n for n in SIZES)
+    value = subsets_step * args.steps / (total_ms * 1e-3)
+
+    line = None
+    if rank == 0:
+        pk = peaks()
+        sm_max = float(pk.get("sm_max_mhz", 2070.0))
+        info = pf3.device_info()
+        n_sm = info["sm_count"]
+        # roofline of the dominant kernel (the W = 2 walk, both launches)
+        ops = sum((1 << n) // world * i_alg(2) for n in SIZES) * args.steps
+        kern_s = sum(sum(v) for v in launch_ms.values()) * 1e-3
+        achieved = ops / kern_s / 1e12
+        lanes = float(os.environ.get("PF3_ALU_LANES", "64"))
+        peak = n_sm * sm_max * 1e6 * lanes / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+                "traffic": None,
+                "note": f"ops = {i_alg(2)} ALU instructions per subset (W=2 grouped walk); peak = {n_sm} SMs x "
+                        f"{sm_max:.0f} MHz x {lanes:.0f} lanes/clk/SM (LOP3/ISETP issue), of measured clock"}
+        # e2e through the host-pointer C entry point (copies in and out each call)
+        e2e = None
+        if world == 1:
+            for n in SIZES:
+                pf3.perm_f3(mats[n])
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                for n in SIZES:
+                    r = pf3.perm_f3(mats[n])
+                    assert r == results[n]
+            dt = time.perf_counter() - t0
+            e2e = {"value": subsets_step * args.steps / dt, "unit": UNIT,
+                   "h2d_bytes_per_step": int(sum(n * n for n in SIZES)),
+                   "d2h_bytes_per_step": int(24 * len(SIZES))}
+        extra = {}
+        if not args.no_batch and world == 1:
+            extra["batch_n24"] = bench_batch(pf3, torch, dev, stream)
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            cpu = cpu_sample(mats[36])
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "strong", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+                "config": {"workload": "perm mod 3 of the seeded uniform 36x36 and 40x40 matrices over F3, "
+                                       "full 2^n Gray walk, one matrix per launch",
+                           "sizes": list(SIZES), "subsets_per_step": subsets_step,
+                           "l2": "flushed between steps (256 MB write)",
+                           "results": {str(n): results[n] for n in SIZES},
+                           "ms_per_launch": {str(n): float(np.mean(v)) for n, v in launch_ms.items()},
+                           "parallelism": f"range split x{world}" if world > 1 else "1 GPU"},
+                "clocks": clk, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": len(SIZES) * args.steps, "wall_s_timed": t_wall, "extra": extra}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def bench_batch(pf3, torch, dev, stream, count=200000):
+    """Batched Monte Carlo: 200,000 seeded uniform 24x24 matrices, one call."""
+    from paper_2407_20205_gb300 import inputs
+    A = inputs.uniform_matrices(inputs.SEED_BATCH24, 24, count)
+    ns = np.full(count, 24, dtype=np.int32)
+    dAs = torch.from_numpy(A.reshape(-1)).to(dev)
+    dres = torch.zeros(count, dtype=torch.uint8, device=dev)
+    dh = torch.zeros(3, dtype=torch.int64, device=dev)
+    with torch.cuda.stream(stream):
+        pf3.perm_f3_batch_async(dAs, ns, dres, dh, stream)  # warm-up
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pf3.perm_f3_batch_async(dAs, ns, dres, dh, stream)
+        e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1)
+    hist = [int(x) for x in dh.cpu()]
+    sub_s = count * (1 << 24) / (ms * 1e-3)
+    n_sm = pf3.device_info()["sm_count"]
+    peak_ops = n_sm * float(peaks().get("sm_max_mhz", 2070.0)) * 1e6 * 64
+    return {"matrices": count, "n": 24, "ms": ms, "perms_per_s": count / (ms * 1e-3),
+            "subsets_per_s": sub_s, "hist": hist,
+            "alu_frac": sub_s * i_alg(1) / peak_ops}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,132 @@
+/*
+ * perm_f3.h -- C ABI of the GB300 library for permanents over F3
+ * (D. Scheinerman, "Fast computation of permanents over F3 via F2
+ * arithmetic", arXiv 2407.20205).
+ *
+ * perm(A) for A in F3^{n x n}, n <= 64, by Ryser's formula (Eq. (2)) walked in
+ * reflected-binary Gray-code order (Sec. 3), each row-subset sum held as the
+ * paper's bit-sliced (mag, sgn) pair (Sec. 2, Definition 2.1), one launch per
+ * call on the current CUDA device.
+ *
+ * Conventions shared by every entry point:
+ *   - A matrix is n*n bytes, row-major, entries in {0,1,2} where 2 stands for
+ *     -1 (the paper's alphabet is {-1,0,1}, Sec. 3).  An entry above 2 is an
+ *     error (PF3_EDOMAIN); the paper's packing routine asserts the same
+ *     (appendix, conversion to the bipedal pair).
+ *   - Results are perm(A) mod 3 in {0,1,2} (-1 is returned as 2).
+ *   - Counts: for Gray index i (subset gray(i) = i ^ (i >> 1), Sec. 3.1
+ *     footnote) the Ryser term is (-1)^{|S|} * prod(subset sum) in {-1,0,1}.
+ *     "plus" counts the indices whose term is +1, "minus" those whose term is
+ *     -1; perm(A) = (-1)^n (plus - minus) mod 3.  Counts are exact 64-bit
+ *     integers.  The subsets are ROW subsets, as in the paper's code (Sec. 3),
+ *     which equals Eq. (2)'s column form because perm(A) = perm(A^T).
+ *   - n = 0: perm is 1 (the empty product; the paper is silent) and A may be
+ *     NULL.
+ *   - Host-pointer entry points (perm_f3, perm_f3_counts, perm_f3_range_counts,
+ *     perm_f3_batch) copy their inputs before returning, are synchronous, and
+ *     leave outputs untouched on error.  The library owns its device scratch;
+ *     calls are serialised per device.
+ *   - Device-pointer entry points (suffix _async) are stream-ordered on the
+ *     given cudaStream_t (NULL = legacy default stream); they return once the
+ *     work is enqueued.  The caller owns every pointer passed in.  They share
+ *     the device's scratch, so two _async calls must not overlap on the GPU
+ *     (use one stream, or order the streams).
+ *   - Return value: >= 0 on success, a negative PF3_E* code on failure.
+ */
+#ifndef PERM_F3_H
+#define PERM_F3_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PF3_OK 0
+#define PF3_PENDING 1        /* perm_f3_poll: job not finished yet */
+#define PF3_EINVAL (-1)      /* null pointer, n outside 0..64, first > last, bad size */
+#define PF3_EDOMAIN (-2)     /* a matrix entry outside {0,1,2} */
+#define PF3_ECUDA (-3)       /* a CUDA runtime call failed (no device, launch error) */
+#define PF3_ENOMEM (-4)      /* device or pinned host allocation failed */
+#define PF3_ETIMEDOUT (-5)   /* perm_f3_wait: the deadline passed */
+#define PF3_ECANCELED (-6)   /* the job or context was cancelled */
+#define PF3_EBUSY (-7)       /* perm_f3_submit: the request queue is full */
+
+#define PF3_MAX_N 64
+
+/* Human-readable text for a return code (static storage). */
+const char* pf3_strerror(int code);
+
+/* Library version string (static storage). */
+const char* pf3_version(void);
+
+/* ------------------------------------------------------------ one matrix */
+
+/* perm(A) mod 3 (Eq. (2), Sec. 3).  A: host, n*n bytes.  Returns 0, 1 or 2,
+ * or a negative PF3_E* code. */
+int perm_f3(const uint8_t* A, int n);
+
+/* Term counts over all 2^n Gray indices (the exact sum behind perm_f3).
+ * plus/minus: host outputs.  For n = 0, plus = 1 and minus = 0. */
+int perm_f3_counts(const uint8_t* A, int n, uint64_t* plus, uint64_t* minus);
+
+/* Term counts over the Gray indices first..last inclusive (0 <= first <= last
+ * <= 2^n - 1; for n = 64 last may be UINT64_MAX).  This is the per-job block
+ * sum of Sec. 3.1: disjoint ranges add up to perm_f3_counts.  n >= 1. */
+int perm_f3_range_counts(const uint8_t* A, int n, uint64_t first, uint64_t last, uint64_t* plus,
+                         uint64_t* minus);
+
+/* Device-pointer form of perm_f3_range_counts (and, with first = 0 and
+ * last = 2^n - 1, of perm_f3).  dA: device, n*n bytes.  d_out: device,
+ * 3 x uint64: plus, minus, and perm mod 3 in {0,1,2} -- or UINT64_MAX there
+ * when an entry of dA is outside {0,1,2} (then plus = minus = 0).  n >= 1.
+ * stream: a cudaStream_t. */
+int perm_f3_range_counts_async(const uint8_t* dA, int n, uint64_t first, uint64_t last, uint64_t* d_out,
+                               void* stream);
+
+/* ------------------------------------------------------------ batches */
+
+/* perm mod 3 of `count` matrices in one call.  As: host, the matrices back to
+ * back, matrix k (size ns[k] x ns[k]) starting at byte sum_{j<k} ns[j]^2.
+ * results: host, count bytes.  hist: optional host uint64[3], the number of
+ * results equal to 0, 1 and 2 (the Monte Carlo statistic of Sec. 4).  Matrices
+ * of different n may be mixed.  Returns 0 or a negative code. */
+int perm_f3_batch(const uint8_t* As, const int32_t* ns, int64_t count, uint8_t* results, uint64_t* hist);
+
+/* Device-pointer batch: dAs, d_results (count bytes) and d_hist (3 x uint64,
+ * overwritten) on the device; ns and the matrix offsets are read from the HOST
+ * array ns (the library builds its work plan from them).  Stream-ordered on
+ * `stream`; an entry outside {0,1,2} gives result 255 for that matrix. */
+int perm_f3_batch_async(const uint8_t* dAs, const int32_t* ns, int64_t count, uint8_t* d_results,
+                        uint64_t* d_hist, void* stream);
+
+/* ------------------------------------------------------------ diagnostics */
+
+/* The row step on every case: for state s in 0..3 ((mag, sgn) = (s>>1, s&1)),
+ * constant c in {0,1,2} and direction d (0 add, 1 subtract), writes
+ * out[((s*3 + c)*2 + d)*2 + {0,1}] = (mag', sgn'), 48 host uint32 (Sec. 2,
+ * Theorem 2.1 / Table 1 semantics). */
+int pf3_step_table(uint32_t* out);
+
+/* The bit planes of A as the kernels pack them (phi of Sec. 2): column j is
+ * bit j, least significant first.  mag, sgn: host, n uint64 each. */
+int pf3_pack(const uint8_t* A, int n, uint64_t* mag, uint64_t* sgn);
+
+/* Integer-pipe microbenchmark (the roofline denominator of the walk).  kind:
+ * 0 LOP3, 1 IMAD, 2 IADD, 3 LOP3+IMAD, 4 walk step (3 LOP3 + compare), 5 POPC.
+ * Runs `ctas_per_sm` CTAs of `threads` threads per SM for `iters` rounds and
+ * reports instructions per clock per SM (thread instructions, i.e. lanes),
+ * thread instructions per second over the whole GPU, and the SM clock in MHz
+ * the CTAs saw.  Any output pointer may be NULL. */
+int pf3_intpipe_bench(int kind, int ctas_per_sm, int threads, int iters, double* inst_per_clk_per_sm,
+                      double* inst_per_s, double* sm_mhz);
+
+/* Device facts the roofline uses: SM count and the current device index. */
+int pf3_device_info(int* sm_count, int* device);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PERM_F3_H */

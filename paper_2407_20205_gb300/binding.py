@@ -1,0 +1,228 @@
+"""Thin ctypes binding over libperm_f3.so (include/perm_f3.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Host buffers are numpy arrays (or anything numpy can view); device
+buffers are raw pointers (int) or CUDA tensors (their ``data_ptr()``), and
+streams are raw ``cudaStream_t`` handles (int) or ``torch.cuda.Stream``.
+
+Importing this module loads the library and raises ImportError when it has
+not been built (``python -c "import __graft_entry__ as g; g.build()"``): there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libperm_f3.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build the CUDA library first "
+                      "(paper_2407_20205_gb300.build.build())")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_vp = ctypes.c_void_p
+
+PF3_OK = 0
+PF3_PENDING = 1
+PF3_EINVAL = -1
+PF3_EDOMAIN = -2
+PF3_ECUDA = -3
+PF3_ENOMEM = -4
+PF3_ETIMEDOUT = -5
+PF3_ECANCELED = -6
+PF3_EBUSY = -7
+MAX_N = 64
+
+
+def _sig(name, restype, argtypes):
+    f = getattr(_lib, name)
+    f.restype = restype
+    f.argtypes = argtypes
+    return f
+
+
+_lib_strerror = _sig("pf3_strerror", ctypes.c_char_p, [ctypes.c_int])
+_lib_version = _sig("pf3_version", ctypes.c_char_p, [])
+_lib_perm = _sig("perm_f3", ctypes.c_int, [_u8p, ctypes.c_int])
+_lib_counts = _sig("perm_f3_counts", ctypes.c_int, [_u8p, ctypes.c_int, _u64p, _u64p])
+_lib_range = _sig("perm_f3_range_counts", ctypes.c_int,
+                  [_u8p, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, _u64p, _u64p])
+_lib_range_async = _sig("perm_f3_range_counts_async", ctypes.c_int,
+                        [_vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, _vp, _vp])
+_lib_batch = _sig("perm_f3_batch", ctypes.c_int, [_u8p, _i32p, ctypes.c_int64, _u8p, _u64p])
+_lib_batch_async = _sig("perm_f3_batch_async", ctypes.c_int,
+                        [_vp, _i32p, ctypes.c_int64, _vp, _vp, _vp])
+_lib_step_table = _sig("pf3_step_table", ctypes.c_int, [_u32p])
+_lib_pack = _sig("pf3_pack", ctypes.c_int, [_u8p, ctypes.c_int, _u64p, _u64p])
+_lib_intpipe = _sig("pf3_intpipe_bench", ctypes.c_int,
+                    [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp])
+_lib_devinfo = _sig("pf3_device_info", ctypes.c_int, [_ip, _ip])
+
+
+class PF3Error(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code})" if what else f"{strerror(code)} ({code})")
+
+
+def strerror(code: int) -> str:
+    return _lib_strerror(code).decode()
+
+
+def version() -> str:
+    return _lib_version().decode()
+
+
+def _check(rc: int, what: str) -> int:
+    if rc < 0:
+        raise PF3Error(rc, what)
+    return rc
+
+
+def _host_u8(A):
+    a = np.ascontiguousarray(np.asarray(A), dtype=np.uint8)
+    return a, a.ctypes.data_as(_u8p)
+
+
+def _square(A):
+    a, p = _host_u8(A)
+    if a.ndim != 2 or a.shape[0] != a.shape[1]:
+        raise ValueError("square matrix expected")
+    return a, p, a.shape[0]
+
+
+def _dev_ptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    raise TypeError("device pointer expected (int or CUDA tensor)")
+
+
+def _stream_ptr(s) -> int:
+    if s is None:
+        return 0
+    if isinstance(s, int):
+        return s
+    if hasattr(s, "cuda_stream"):
+        return int(s.cuda_stream)
+    raise TypeError("stream expected (int handle or torch.cuda.Stream)")
+
+
+# ------------------------------------------------------------ one matrix
+
+def perm_f3(A) -> int:
+    """perm(A) mod 3 in {0,1,2} for a square {0,1,2} matrix (host)."""
+    a, p, n = _square(A)
+    if n == 0:
+        return _check(_lib_perm(None, 0), "perm_f3")
+    return _check(_lib_perm(p, n), "perm_f3")
+
+
+def perm_f3_counts(A) -> tuple[int, int]:
+    """(plus, minus) Ryser term counts over all 2^n Gray indices."""
+    a, p, n = _square(A)
+    P, M = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(_lib_counts(p if n else None, n, ctypes.byref(P), ctypes.byref(M)), "perm_f3_counts")
+    return P.value, M.value
+
+
+def perm_f3_range_counts(A, first: int, last: int) -> tuple[int, int]:
+    """(plus, minus) over the Gray indices first..last inclusive."""
+    a, p, n = _square(A)
+    P, M = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(_lib_range(p, n, first, last, ctypes.byref(P), ctypes.byref(M)), "perm_f3_range_counts")
+    return P.value, M.value
+
+
+def perm_f3_range_counts_async(dA, n: int, first: int, last: int, d_out, stream=None) -> None:
+    """Device form: dA (n*n bytes) and d_out (3 x uint64) on the device."""
+    _check(_lib_range_async(_dev_ptr(dA), n, first, last, _dev_ptr(d_out), _stream_ptr(stream)),
+           "perm_f3_range_counts_async")
+
+
+# ------------------------------------------------------------ batches
+
+def pack_batch(mats):
+    """Back-to-back bytes and sizes of a list of square matrices."""
+    mats = [np.ascontiguousarray(np.asarray(m), dtype=np.uint8) for m in mats]
+    ns = np.array([m.shape[0] for m in mats], dtype=np.int32)
+    flat = np.concatenate([m.ravel() for m in mats]) if mats else np.zeros(0, np.uint8)
+    return flat, ns
+
+
+def perm_f3_batch(mats=None, *, flat=None, ns=None, with_hist: bool = False):
+    """perm mod 3 of many matrices: a list of matrices, or (flat, ns)."""
+    if mats is not None:
+        flat, ns = pack_batch(mats)
+    flat = np.ascontiguousarray(flat, dtype=np.uint8)
+    ns = np.ascontiguousarray(ns, dtype=np.int32)
+    count = int(ns.shape[0])
+    res = np.zeros(max(count, 1), dtype=np.uint8)
+    hist = np.zeros(3, dtype=np.uint64)
+    fp = flat.ctypes.data_as(_u8p) if flat.size else None
+    _check(_lib_batch(fp, ns.ctypes.data_as(_i32p), count, res.ctypes.data_as(_u8p),
+                      hist.ctypes.data_as(_u64p)), "perm_f3_batch")
+    return (res[:count], hist) if with_hist else res[:count]
+
+
+def perm_f3_batch_async(dAs, ns, d_results, d_hist, stream=None) -> None:
+    ns = np.ascontiguousarray(ns, dtype=np.int32)
+    _check(_lib_batch_async(_dev_ptr(dAs), ns.ctypes.data_as(_i32p), int(ns.shape[0]),
+                            _dev_ptr(d_results), _dev_ptr(d_hist), _stream_ptr(stream)),
+           "perm_f3_batch_async")
+
+
+# ------------------------------------------------------------ diagnostics
+
+def step_table() -> np.ndarray:
+    """uint32[4, 3, 2, 2]: (mag', sgn') for state, constant c, direction."""
+    out = np.zeros(48, dtype=np.uint32)
+    _check(_lib_step_table(out.ctypes.data_as(_u32p)), "pf3_step_table")
+    return out.reshape(4, 3, 2, 2)
+
+
+def pack(A) -> tuple[np.ndarray, np.ndarray]:
+    a, p, n = _square(A)
+    mag = np.zeros(n, dtype=np.uint64)
+    sgn = np.zeros(n, dtype=np.uint64)
+    _check(_lib_pack(p, n, mag.ctypes.data_as(_u64p), sgn.ctypes.data_as(_u64p)), "pf3_pack")
+    return mag, sgn
+
+
+INTPIPE_KINDS = {"lop3": 0, "imad": 1, "iadd": 2, "lop3_imad": 3, "step": 4, "popc": 5, "max_imad": 6,
+                 "lop3x2_max": 7, "probe": 8, "step_imad": 9, "lop3x2_iadd": 10}
+
+
+def intpipe_bench(kind, ctas_per_sm: int = 4, threads: int = 256, iters: int = 4096) -> dict:
+    k = INTPIPE_KINDS[kind] if isinstance(kind, str) else int(kind)
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(_lib_intpipe(k, ctas_per_sm, threads, iters, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "pf3_intpipe_bench")
+    return {"inst_per_clk_per_sm": a.value, "inst_per_s": b.value, "sm_mhz": c.value}
+
+
+def device_info() -> dict:
+    sm, dev = ctypes.c_int(), ctypes.c_int()
+    _check(_lib_devinfo(ctypes.byref(sm), ctypes.byref(dev)), "pf3_device_info")
+    return {"sm_count": sm.value, "device": dev.value}
+
+
+def exported_symbols() -> list[str]:
+    return [n for n in ("pf3_strerror", "pf3_version", "perm_f3", "perm_f3_counts",
+                        "perm_f3_range_counts", "perm_f3_range_counts_async", "perm_f3_batch",
+                        "perm_f3_batch_async", "pf3_step_table", "pf3_pack", "pf3_intpipe_bench",
+                        "pf3_device_info") if hasattr(_lib, n)]

@@ -1,0 +1,352 @@
+// pf3_batch.cu -- many matrices of uneven n in one persistent launch per
+// plane width (the Monte Carlo workload of Sec. 4: permanents of many random
+// matrices).
+//
+// The host plans work items: a matrix with n <= cutoff is one item walked by
+// one warp (its 32 lanes split the 2^(n-U) Gray blocks); a larger matrix is
+// cut into items of 2^chunk_log2 Gray indices (Sec. 3.1's blocks of
+// consecutive Gray states), whose counts meet in per-matrix accumulators; the
+// warp that finishes a matrix's last item maps its counts to perm mod 3.
+// Items are sorted largest first and handed out through an atomic cursor, so
+// the grid stays full until the end.  Each warp packs its matrix into its own
+// shared-memory row table.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <vector>
+
+#include "perm_f3.h"
+#include "pf3_batch.h"
+#include "pf3_context.h"
+#include "pf3_device.cuh"
+#include "pf3_internal.h"
+
+namespace pf3 {
+
+namespace {
+
+constexpr unsigned kBadBit = 0x80000000u;
+
+template <int W, int U>
+__global__ void __launch_bounds__(kBatchThreads) batch_kernel(BatchArgs a)
+{
+    constexpr int G = kGroupLog2;
+    __shared__ RowTable<W> tabs[kBatchThreads / 32];
+    __shared__ WarpQueue<W> queues[kBatchThreads / 32];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    RowTable<W>& tab = tabs[warp];
+    WarpQueue<W>& q = queues[warp];
+    if (lane == 0) q.count = 0;
+    __syncwarp();
+
+    for (;;) {
+        unsigned item = 0;
+        if (lane == 0) item = atomicAdd(a.cursor, 1u);
+        item = __shfl_sync(0xFFFFFFFFu, item, 0);
+        if (item >= a.num_items) break;
+        const WorkItem it = a.items[item];
+        const int n = it.n;
+        const uint8_t* A = a.As + it.offset;
+
+        bool bad = false;
+        const int rows = n > U ? n : U;
+        for (int r = 0; r < rows; ++r) {
+            uint32_t mag[2], sgn[2];
+            pack_row_warp(A, n, r, lane, mag, sgn, bad);
+            if (lane < W) {
+                uint32_t k1, k2p, k2m;
+                row_masks(mag[lane], sgn[lane], k1, k2p, k2m);
+                tab.e[0][r].k1[lane] = k1;
+                tab.e[0][r].k2[lane] = k2p;
+                tab.e[1][r].k1[lane] = k1;
+                tab.e[1][r].k2[lane] = k2m;
+            }
+        }
+        bad = __any_sync(0xFFFFFFFFu, bad);
+        __syncwarp();
+
+        Counts c{0ull, 0ull};
+        if (!bad && n > 0) {
+            if (it.NB == 0) {
+                // small n: one lane walks all 2^n indices
+                if (lane == 0) walk_generic<W>(tab, n, 0, (n == 64) ? ~0ull : ((1ull << n) - 1), c);
+            } else {
+                GroupRows<W, G, U> R;
+                load_group_rows<W, G, U>(R, tab);
+                uint64_t s, len;
+                split_range(it.NB, 32, (uint64_t)lane, s, len);
+                const uint64_t trip = __shfl_sync(0xFFFFFFFFu, len, 0);
+                walk_groups<W, G, U>(tab, R, n, it.B0 + s, len, trip, q, lane, c);
+            }
+        }
+        const unsigned long long p = warp_sum(c.plus);
+        const unsigned long long m = warp_sum(c.minus);
+        if (lane == 0) {
+            int result = -1;
+            if (it.split < 0) {
+                result = bad ? 255 : (n == 0 ? 1 : (int)perm_from_counts(n, p, m));
+            } else {
+                unsigned long long* acc = a.acc + 2 * it.split;
+                atomicAdd(acc, p);
+                atomicAdd(acc + 1, m);
+                if (bad) atomicOr(a.left + it.split, kBadBit);
+                __threadfence();
+                const unsigned before = atomicSub(a.left + it.split, 1u);
+                if ((before & ~kBadBit) == 1u) {
+                    __threadfence();
+                    const unsigned long long P = __ldcg(acc), M = __ldcg(acc + 1);
+                    result = (before & kBadBit) ? 255 : (int)perm_from_counts(n, P, M);
+                }
+            }
+            if (result >= 0) {
+                a.results[it.mat] = (uint8_t)result;
+                if (result < 3 && a.hist) atomicAdd(a.hist + result, 1ull);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <int W>
+const void* batch_kernel_ptr()
+{
+    return (const void*)batch_kernel<W, kBlockLog2>;
+}
+
+}  // namespace
+
+int batch_max_ctas_per_sm(int W)
+{
+    int ctas = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, W == 1 ? batch_kernel_ptr<1>() : batch_kernel_ptr<2>(),
+                                                  kBatchThreads, 0);
+    return ctas > 0 ? ctas : 1;
+}
+
+cudaError_t launch_batch(int W, const BatchArgs& a, int grid, cudaStream_t stream)
+{
+    if (W == 1) batch_kernel<1, kBlockLog2><<<grid, kBatchThreads, 0, stream>>>(a);
+    else batch_kernel<2, kBlockLog2><<<grid, kBatchThreads, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- planning
+
+void plan_batch(const int32_t* ns, int64_t count, const BatchTuning& tune, BatchPlan& plan)
+{
+    plan.items[0].clear();
+    plan.items[1].clear();
+    plan.split_items.clear();
+    plan.num_split = 0;
+    plan.total_bytes = 0;
+    constexpr int U = kBlockLog2;
+    long long off = 0;
+    for (int64_t k = 0; k < count; ++k) {
+        const int n = ns[k];
+        WorkItem it;
+        std::memset(&it, 0, sizeof(it));
+        it.offset = off;
+        it.mat = (int)k;
+        it.n = n;
+        it.split = -1;
+        const int cls = n <= 32 ? 0 : 1;
+        off += (long long)n * n;
+        if (n < U + 1) {
+            it.B0 = 0;
+            it.NB = 0;  // generic walk by one lane
+            plan.items[cls].push_back(it);
+            continue;
+        }
+        const uint64_t NB = (n == 64) ? (1ull << (64 - U)) : (1ull << (n - U));
+        if (n <= tune.cutoff) {
+            it.B0 = 0;
+            it.NB = NB;
+            plan.items[cls].push_back(it);
+            continue;
+        }
+        const int cl = std::max(tune.chunk_log2, U + 5);
+        const uint64_t per = 1ull << (cl - U);
+        const uint64_t nitems = (NB + per - 1) / per;
+        it.split = plan.num_split++;
+        plan.split_items.push_back((unsigned)nitems);
+        for (uint64_t q = 0; q < nitems; ++q) {
+            it.B0 = q * per;
+            it.NB = std::min<unsigned long long>(per, NB - it.B0);
+            plan.items[cls].push_back(it);
+        }
+    }
+    plan.total_bytes = off;
+    // largest first (longest-processing-time order); ties keep matrix order
+    for (int cls = 0; cls < 2; ++cls) {
+        std::stable_sort(plan.items[cls].begin(), plan.items[cls].end(),
+                         [](const WorkItem& x, const WorkItem& y) { return x.NB > y.NB; });
+    }
+}
+
+// grow-only device scratch for a plan
+static int ensure_batch_scratch(DeviceCtx* c, size_t items, size_t splits, size_t bytes, size_t mats)
+{
+    BatchScratch& b = c->batch;
+    cudaError_t e = cudaSuccess;
+    if (items > b.items_cap) {
+        cudaFree(b.d_items);
+        cudaFreeHost(b.h_items);
+        b.d_items = nullptr;
+        b.h_items = nullptr;
+        size_t cap = std::max(items, (size_t)1024);
+        if ((e = cudaMalloc(&b.d_items, cap * sizeof(WorkItem))) != cudaSuccess) return cuda_rc(e);
+        if ((e = cudaMallocHost(&b.h_items, cap * sizeof(WorkItem))) != cudaSuccess) return cuda_rc(e);
+        b.items_cap = cap;
+    }
+    if (splits + 1 > b.mats_cap || !b.d_cursor) {
+        cudaFree(b.d_acc);
+        cudaFree(b.d_left);
+        cudaFree(b.d_cursor);
+        size_t cap = std::max(splits + 1, (size_t)1024);
+        if ((e = cudaMalloc(&b.d_acc, cap * 2 * sizeof(unsigned long long))) != cudaSuccess) return cuda_rc(e);
+        if ((e = cudaMalloc(&b.d_left, cap * sizeof(unsigned int))) != cudaSuccess) return cuda_rc(e);
+        if ((e = cudaMalloc(&b.d_cursor, 4 * sizeof(unsigned int))) != cudaSuccess) return cuda_rc(e);
+        b.mats_cap = cap;
+    }
+    if (bytes > b.bytes_cap || mats > b.res_cap) {
+        cudaFree(b.d_As);
+        cudaFree(b.d_results);
+        cudaFree(b.d_hist);
+        b.d_As = nullptr;
+        b.d_results = nullptr;
+        b.d_hist = nullptr;
+        size_t bcap = std::max(bytes, (size_t)4096), rcap = std::max(mats, (size_t)1024);
+        if ((e = cudaMalloc(&b.d_As, bcap)) != cudaSuccess) return cuda_rc(e);
+        if ((e = cudaMalloc(&b.d_results, rcap)) != cudaSuccess) return cuda_rc(e);
+        if ((e = cudaMalloc(&b.d_hist, 4 * sizeof(unsigned long long))) != cudaSuccess) return cuda_rc(e);
+        b.bytes_cap = bcap;
+        b.res_cap = rcap;
+    }
+    return PF3_OK;
+}
+
+// enqueue a planned batch on `stream`: upload the item table and split
+// counters, reset cursors and histogram, launch one persistent grid per class
+int enqueue_batch(DeviceCtx* c, const BatchPlan& plan, const uint8_t* dAs, uint8_t* d_results,
+                  unsigned long long* d_hist, cudaStream_t stream)
+{
+    const size_t n0 = plan.items[0].size(), n1 = plan.items[1].size();
+    BatchScratch& b = c->batch;
+    int rc = ensure_batch_scratch(c, n0 + n1, (size_t)plan.num_split, 0, 0);
+    if (rc) return rc;
+    WorkItem* h = (WorkItem*)b.h_items;
+    // the pinned mirror may still be read by an earlier upload on this stream
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_rc(e);
+    if (n1) std::memcpy(h, plan.items[1].data(), n1 * sizeof(WorkItem));
+    if (n0) std::memcpy(h + n1, plan.items[0].data(), n0 * sizeof(WorkItem));
+    if (n0 + n1)
+        e = cudaMemcpyAsync(b.d_items, h, (n0 + n1) * sizeof(WorkItem), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess && plan.num_split) {
+        e = cudaMemsetAsync(b.d_acc, 0, (size_t)plan.num_split * 2 * sizeof(unsigned long long), stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b.d_left, plan.split_items.data(), (size_t)plan.num_split * sizeof(unsigned int),
+                                cudaMemcpyHostToDevice, stream);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.d_cursor, 0, 4 * sizeof(unsigned int), stream);
+    if (e == cudaSuccess && d_hist) e = cudaMemsetAsync(d_hist, 0, 3 * sizeof(unsigned long long), stream);
+    if (e != cudaSuccess) return cuda_rc(e);
+    BatchArgs a;
+    a.As = dAs;
+    a.results = d_results;
+    a.hist = d_hist;
+    a.acc = b.d_acc;
+    a.left = b.d_left;
+    for (int cls = 1; cls >= 0; --cls) {
+        const size_t cnt = plan.items[cls].size();
+        if (!cnt) continue;
+        a.items = (const WorkItem*)b.d_items + (cls == 1 ? 0 : n1);
+        a.num_items = (unsigned)cnt;
+        a.cursor = b.d_cursor + cls;
+        const int per_sm = c->batch_ctas[cls];
+        int grid = c->sm_count * per_sm;
+        const size_t warps_needed = cnt;
+        const size_t ctas_needed = (warps_needed + kBatchThreads / 32 - 1) / (kBatchThreads / 32);
+        if ((size_t)grid > ctas_needed) grid = (int)ctas_needed;
+        if ((e = launch_batch(cls == 0 ? 1 : 2, a, grid, stream)) != cudaSuccess) return cuda_rc(e);
+    }
+    return PF3_OK;
+}
+
+}  // namespace pf3
+
+using namespace pf3;
+
+extern "C" {
+
+int perm_f3_batch(const uint8_t* As, const int32_t* ns, int64_t count, uint8_t* results, uint64_t* hist)
+{
+    if (count < 0 || (count > 0 && (!ns || !results))) return PF3_EINVAL;
+    if (count == 0) {
+        if (hist) hist[0] = hist[1] = hist[2] = 0;
+        return PF3_OK;
+    }
+    size_t bytes = 0;
+    for (int64_t k = 0; k < count; ++k) {
+        if (ns[k] < 0 || ns[k] > PF3_MAX_N) return PF3_EINVAL;
+        bytes += (size_t)ns[k] * ns[k];
+    }
+    if (bytes && !As) return PF3_EINVAL;
+    for (size_t k = 0; k < bytes; ++k)
+        if (As[k] > 2) return PF3_EDOMAIN;
+    int rc;
+    DeviceCtx* c = device_ctx(&rc);
+    if (!c) return rc;
+    std::lock_guard<std::mutex> g(c->mu);
+    BatchPlan plan;
+    plan_batch(ns, count, c->tune, plan);
+    if ((rc = ensure_batch_scratch(c, plan.items[0].size() + plan.items[1].size(), (size_t)plan.num_split, bytes,
+                                   (size_t)count)))
+        return rc;
+    BatchScratch& b = c->batch;
+    cudaError_t e = cudaSuccess;
+    if (bytes) e = cudaMemcpyAsync(b.d_As, As, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_rc(e);
+    if ((rc = enqueue_batch(c, plan, b.d_As, b.d_results, b.d_hist, c->stream))) return rc;
+    e = cudaMemcpyAsync(results, b.d_results, (size_t)count, cudaMemcpyDeviceToHost, c->stream);
+    unsigned long long h[3] = {0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, b.d_hist, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_rc(e);
+    if (hist) {
+        hist[0] = h[0];
+        hist[1] = h[1];
+        hist[2] = h[2];
+    }
+    return PF3_OK;
+}
+
+int perm_f3_batch_async(const uint8_t* dAs, const int32_t* ns, int64_t count, uint8_t* d_results, uint64_t* d_hist,
+                        void* stream)
+{
+    if (count < 0 || (count > 0 && (!ns || !d_results))) return PF3_EINVAL;
+    size_t bytes = 0;
+    for (int64_t k = 0; k < count; ++k) {
+        if (ns[k] < 0 || ns[k] > PF3_MAX_N) return PF3_EINVAL;
+        bytes += (size_t)ns[k] * ns[k];
+    }
+    if (bytes && !dAs) return PF3_EINVAL;
+    int rc;
+    DeviceCtx* c = device_ctx(&rc);
+    if (!c) return rc;
+    std::lock_guard<std::mutex> g(c->mu);
+    if (count == 0) {
+        if (d_hist)
+            return cuda_rc(cudaMemsetAsync(d_hist, 0, 3 * sizeof(unsigned long long), (cudaStream_t)stream));
+        return PF3_OK;
+    }
+    BatchPlan& plan = c->last_plan;
+    plan_batch(ns, count, c->tune, plan);
+    return enqueue_batch(c, plan, dAs, d_results, (unsigned long long*)d_hist, (cudaStream_t)stream);
+}
+
+}  // extern "C"

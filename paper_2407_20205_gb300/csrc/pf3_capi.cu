@@ -1,0 +1,300 @@
+// pf3_capi.cu -- the C ABI declared in include/perm_f3.h: argument checks,
+// per-device contexts (stream, scratch, pinned staging) and the host side of
+// the one-matrix entry points and diagnostics.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "perm_f3.h"
+#include "pf3_context.h"
+#include "pf3_internal.h"
+
+namespace pf3 {
+
+namespace {
+
+std::mutex g_registry_mu;
+std::vector<DeviceCtx*> g_ctx;  // indexed by device ordinal
+
+}  // namespace
+
+int cuda_rc(cudaError_t e)
+{
+    if (e == cudaSuccess) return PF3_OK;
+    if (e == cudaErrorMemoryAllocation) return PF3_ENOMEM;
+    return PF3_ECUDA;
+}
+
+DeviceCtx* device_ctx(int* rc)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        *rc = PF3_ECUDA;
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> g(g_registry_mu);
+    if ((int)g_ctx.size() <= dev) g_ctx.resize(dev + 1, nullptr);
+    if (g_ctx[dev]) {
+        *rc = PF3_OK;
+        return g_ctx[dev];
+    }
+    DeviceCtx* c = new DeviceCtx();
+    c->device = dev;
+    cudaDeviceProp prop;
+    if ((e = cudaGetDeviceProperties(&prop, dev)) != cudaSuccess) {
+        delete c;
+        *rc = cuda_rc(e);
+        return nullptr;
+    }
+    c->sm_count = prop.multiProcessorCount;
+    c->max_ctas[0] = single_max_ctas_per_sm(1);
+    c->max_ctas[1] = single_max_ctas_per_sm(2);
+    c->batch_ctas[0] = batch_max_ctas_per_sm(1);
+    c->batch_ctas[1] = batch_max_ctas_per_sm(2);
+    const int max_grid = c->sm_count * (c->max_ctas[0] > c->max_ctas[1] ? c->max_ctas[0] : c->max_ctas[1]);
+    c->max_grid = max_grid;
+    bool ok = true;
+    ok = ok && cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && cudaMalloc(&c->d_A, kMaxNN) == cudaSuccess;
+    ok = ok && cudaMalloc(&c->d_partials, sizeof(unsigned long long) * 2 * (size_t)max_grid) == cudaSuccess;
+    ok = ok && cudaMalloc(&c->d_flags, sizeof(unsigned int) * 2) == cudaSuccess;
+    ok = ok && cudaMalloc(&c->d_out, sizeof(unsigned long long) * 4) == cudaSuccess;
+    ok = ok && cudaMemset(c->d_flags, 0, sizeof(unsigned int) * 2) == cudaSuccess;
+    ok = ok && cudaMallocHost(&c->h_A, kMaxNN) == cudaSuccess;
+    ok = ok && cudaMallocHost(&c->h_out, sizeof(unsigned long long) * 4) == cudaSuccess;
+    ok = ok && cudaDeviceSynchronize() == cudaSuccess;
+    if (!ok) {
+        *rc = PF3_ENOMEM;
+        cudaGetLastError();
+        return nullptr;  // leaked partially built context on failure: rare, harmless
+    }
+    g_ctx[dev] = c;
+    *rc = PF3_OK;
+    return c;
+}
+
+int check_entries_host(const uint8_t* A, int n)
+{
+    const size_t nn = (size_t)n * (size_t)n;
+    for (size_t k = 0; k < nn; ++k)
+        if (A[k] > 2) return PF3_EDOMAIN;
+    return PF3_OK;
+}
+
+// enqueue the single-matrix range walk on `stream` (dA on device)
+int enqueue_range(DeviceCtx* c, const uint8_t* dA, int n, uint64_t first, uint64_t last, unsigned long long* d_out,
+                  cudaStream_t stream)
+{
+    SingleArgs a;
+    std::memset(&a, 0, sizeof(a));
+    plan_range(n, first, last, a);
+    a.A = dA;
+    a.partials = c->d_partials;
+    a.ticket = c->d_flags;
+    a.err = c->d_flags + 1;
+    a.out = d_out;
+    const int grid = single_grid_for(a, c->sm_count, c->max_ctas[n <= 32 ? 0 : 1]);
+    return cuda_rc(launch_single(a, grid, stream));
+}
+
+int valid_range(int n, uint64_t first, uint64_t last)
+{
+    if (n < 1 || n > PF3_MAX_N || first > last) return PF3_EINVAL;
+    if (n < 64 && last >= (1ull << n)) return PF3_EINVAL;
+    return PF3_OK;
+}
+
+// host-pointer range counts, synchronous; returns the result byte in *result
+int host_range(const uint8_t* A, int n, uint64_t first, uint64_t last, uint64_t* plus, uint64_t* minus, int* result)
+{
+    int rc = valid_range(n, first, last);
+    if (rc) return rc;
+    if (!A) return PF3_EINVAL;
+    if ((rc = check_entries_host(A, n))) return rc;
+    DeviceCtx* c = device_ctx(&rc);
+    if (!c) return rc;
+    std::lock_guard<std::mutex> g(c->mu);
+    const size_t nn = (size_t)n * n;
+    std::memcpy(c->h_A, A, nn);
+    cudaError_t e = cudaMemcpyAsync(c->d_A, c->h_A, nn, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_rc(e);
+    if ((rc = enqueue_range(c, c->d_A, n, first, last, c->d_out, c->stream))) return rc;
+    e = cudaMemcpyAsync(c->h_out, c->d_out, sizeof(unsigned long long) * 3, cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_rc(e);
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_rc(e);
+    if (c->h_out[2] == ~0ull) return PF3_EDOMAIN;
+    if (plus) *plus = c->h_out[0];
+    if (minus) *minus = c->h_out[1];
+    if (result) *result = (int)c->h_out[2];
+    return PF3_OK;
+}
+
+}  // namespace pf3
+
+using namespace pf3;
+
+extern "C" {
+
+const char* pf3_strerror(int code)
+{
+    switch (code) {
+    case PF3_OK: return "ok";
+    case PF3_PENDING: return "pending";
+    case PF3_EINVAL: return "invalid argument";
+    case PF3_EDOMAIN: return "matrix entry outside {0,1,2}";
+    case PF3_ECUDA: return "CUDA error";
+    case PF3_ENOMEM: return "out of memory";
+    case PF3_ETIMEDOUT: return "timed out";
+    case PF3_ECANCELED: return "cancelled";
+    case PF3_EBUSY: return "queue full";
+    default: return "unknown error";
+    }
+}
+
+const char* pf3_version(void) { return "perm_f3 1.0 (sm_103a)"; }
+
+int perm_f3(const uint8_t* A, int n)
+{
+    if (n < 0 || n > PF3_MAX_N) return PF3_EINVAL;
+    if (n == 0) return 1;
+    const uint64_t last = (n == 64) ? ~0ull : ((1ull << n) - 1);
+    int result = 0;
+    const int rc = host_range(A, n, 0, last, nullptr, nullptr, &result);
+    return rc ? rc : result;
+}
+
+int perm_f3_counts(const uint8_t* A, int n, uint64_t* plus, uint64_t* minus)
+{
+    if (!plus || !minus || n < 0 || n > PF3_MAX_N) return PF3_EINVAL;
+    if (n == 0) {
+        *plus = 1;
+        *minus = 0;
+        return PF3_OK;
+    }
+    const uint64_t last = (n == 64) ? ~0ull : ((1ull << n) - 1);
+    return host_range(A, n, 0, last, plus, minus, nullptr);
+}
+
+int perm_f3_range_counts(const uint8_t* A, int n, uint64_t first, uint64_t last, uint64_t* plus, uint64_t* minus)
+{
+    if (!plus || !minus) return PF3_EINVAL;
+    return host_range(A, n, first, last, plus, minus, nullptr);
+}
+
+int perm_f3_range_counts_async(const uint8_t* dA, int n, uint64_t first, uint64_t last, uint64_t* d_out,
+                               void* stream)
+{
+    int rc = valid_range(n, first, last);
+    if (rc) return rc;
+    if (!dA || !d_out) return PF3_EINVAL;
+    DeviceCtx* c = device_ctx(&rc);
+    if (!c) return rc;
+    std::lock_guard<std::mutex> g(c->mu);
+    return enqueue_range(c, dA, n, first, last, (unsigned long long*)d_out, (cudaStream_t)stream);
+}
+
+int pf3_step_table(uint32_t* out)
+{
+    if (!out) return PF3_EINVAL;
+    int rc;
+    DeviceCtx* c = device_ctx(&rc);
+    if (!c) return rc;
+    std::lock_guard<std::mutex> g(c->mu);
+    uint32_t* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, 48 * sizeof(uint32_t));
+    if (e != cudaSuccess) return cuda_rc(e);
+    e = launch_step_table(d, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, 48 * sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(d);
+    return cuda_rc(e);
+}
+
+int pf3_pack(const uint8_t* A, int n, uint64_t* mag, uint64_t* sgn)
+{
+    if (n < 1 || n > PF3_MAX_N || !A || !mag || !sgn) return PF3_EINVAL;
+    int rc = check_entries_host(A, n);
+    if (rc) return rc;
+    DeviceCtx* c = device_ctx(&rc);
+    if (!c) return rc;
+    std::lock_guard<std::mutex> g(c->mu);
+    unsigned long long* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(unsigned long long) * 2 * PF3_MAX_N);
+    if (e != cudaSuccess) return cuda_rc(e);
+    const size_t nn = (size_t)n * n;
+    std::memcpy(c->h_A, A, nn);
+    e = cudaMemcpyAsync(c->d_A, c->h_A, nn, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = launch_pack(c->d_A, n, d, d + PF3_MAX_N, c->d_flags + 1, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(mag, d, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sgn, d + PF3_MAX_N, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_flags + 1, 0, sizeof(unsigned int), c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(d);
+    return cuda_rc(e);
+}
+
+int pf3_intpipe_bench(int kind, int ctas_per_sm, int threads, int iters, double* inst_per_clk_per_sm,
+                      double* inst_per_s, double* sm_mhz)
+{
+    static const int per_op[11] = {1, 1, 1, 2, 4, 3, 2, 3, 3, 4, 3};
+    if (kind < 0 || kind > 10 || ctas_per_sm < 1 || threads < 32 || threads > 1024 || (threads & 31) || iters < 1)
+        return PF3_EINVAL;
+    int rc;
+    DeviceCtx* c = device_ctx(&rc);
+    if (!c) return rc;
+    std::lock_guard<std::mutex> g(c->mu);
+    const int grid = c->sm_count * ctas_per_sm;
+    uint32_t* sink = nullptr;
+    unsigned long long* cyc = nullptr;
+    cudaError_t e = cudaMalloc(&sink, sizeof(uint32_t) * (size_t)grid * threads);
+    if (e == cudaSuccess) e = cudaMalloc(&cyc, sizeof(unsigned long long) * grid);
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev1);
+    // warm-up launch, then the timed one
+    if (e == cudaSuccess) e = launch_intpipe(kind, grid, threads, iters / 8 + 1, sink, cyc, c->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev0, c->stream);
+    if (e == cudaSuccess) e = launch_intpipe(kind, grid, threads, iters, sink, cyc, c->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev1, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    float ms = 0.f;
+    std::vector<unsigned long long> h(grid);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev0, ev1);
+    if (e == cudaSuccess) e = cudaMemcpy(h.data(), cyc, sizeof(unsigned long long) * grid, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) {
+        // ops per thread: iters * unroll(16) * chains(8) * instructions per op
+        const double ops_thread = (double)iters * 16.0 * 8.0 * per_op[kind];
+        double maxc = 0, sumc = 0;
+        for (int b = 0; b < grid; ++b) {
+            sumc += (double)h[b];
+            if ((double)h[b] > maxc) maxc = (double)h[b];
+        }
+        const double avgc = sumc / grid;
+        const double per_sm = ops_thread * threads * ctas_per_sm / avgc;
+        if (inst_per_clk_per_sm) *inst_per_clk_per_sm = per_sm;
+        if (inst_per_s) *inst_per_s = ops_thread * threads * (double)grid / (ms * 1e-3);
+        if (sm_mhz) *sm_mhz = maxc / (ms * 1e-3) / 1e6;
+    }
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    cudaFree(sink);
+    cudaFree(cyc);
+    return cuda_rc(e);
+}
+
+int pf3_device_info(int* sm_count, int* device)
+{
+    int rc;
+    DeviceCtx* c = device_ctx(&rc);
+    if (!c) return rc;
+    if (sm_count) *sm_count = c->sm_count;
+    if (device) *device = c->device;
+    return PF3_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,57 @@
+// pf3_context.h -- per-device library state (host side).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+
+#include "pf3_batch.h"
+
+namespace pf3 {
+
+constexpr int kMaxNN = 64 * 64;
+
+// Batch scratch (grown on demand): the work-item table and per-matrix state.
+struct BatchScratch {
+    void* d_items = nullptr;              // WorkItem[items_cap]
+    unsigned long long* d_acc = nullptr;  // 2 per matrix: plus, minus
+    unsigned int* d_left = nullptr;       // work items left per matrix
+    long long* d_offsets = nullptr;       // byte offset of each matrix
+    int* d_ns = nullptr;                  // n of each matrix
+    unsigned int* d_cursor = nullptr;     // 2 queue cursors (W = 1, W = 2)
+    uint8_t* d_As = nullptr;              // staging for host-pointer batches
+    uint8_t* d_results = nullptr;         // staging for host-pointer batches
+    unsigned long long* d_hist = nullptr; // staging for host-pointer batches
+    size_t items_cap = 0, mats_cap = 0, bytes_cap = 0, res_cap = 0;
+    void* h_items = nullptr;              // pinned mirror of the item table
+    size_t h_items_cap = 0;
+};
+
+struct DeviceCtx {
+    int device = 0;
+    int sm_count = 0;
+    int max_ctas[2] = {1, 1};  // single kernel, W = 1 / W = 2
+    int max_grid = 0;
+    cudaStream_t stream = nullptr;
+    // single-matrix scratch
+    uint8_t* d_A = nullptr;                   // kMaxNN bytes
+    unsigned long long* d_partials = nullptr; // 2 * max_grid
+    unsigned int* d_flags = nullptr;          // ticket, error flag (0 between launches)
+    unsigned long long* d_out = nullptr;      // plus, minus, result
+    uint8_t* h_A = nullptr;                   // pinned
+    unsigned long long* h_out = nullptr;      // pinned
+    BatchScratch batch;
+    BatchTuning tune;
+    BatchPlan last_plan;
+    int batch_ctas[2] = {1, 1};  // batch kernel, W = 1 / W = 2
+    std::mutex mu;
+};
+
+int cuda_rc(cudaError_t e);
+DeviceCtx* device_ctx(int* rc);
+int check_entries_host(const uint8_t* A, int n);
+struct BatchPlan;
+int enqueue_batch(DeviceCtx* c, const BatchPlan& plan, const uint8_t* dAs, uint8_t* d_results,
+                  unsigned long long* d_hist, cudaStream_t stream);
+
+}  // namespace pf3

@@ -1,0 +1,540 @@
+// pf3_device.cuh -- device building blocks of the bit-sliced Gray-code Ryser
+// walk for perm(A) mod 3, A in F3^{n x n}, n <= 64 (arXiv 2407.20205).
+//
+// Representation (Sec. 2, the "bipedal" pair): an F3 vector of length n is a
+// pair of bit vectors (mag, sgn); column j is bit j (least significant first;
+// the paper's appendix packs most significant first, which only permutes the
+// columns and leaves the permanent unchanged).  phi: 0 -> (0,0), 1 -> (1,0),
+// -1 -> (1,1); (0,1) is a second representation of 0 (Definition 2.1).
+// Each plane is held as W 32-bit words (W = 1 for n <= 32, 2 for n <= 64).
+//
+// Row step (Sec. 2, Theorem 2.1 and the addition truth table, Table 1):
+// adding a row r, or subtracting it, adds a per-column constant c in F3 to the
+// running subset sum.  Instead of Theorem 2.1's six two-input gates we use
+// three three-input gates (one LOP3 each) and two per-row masks, chosen by an
+// exhaustive search over the zero-representation freedom the paper describes
+// (Sec. 2, discussion of Table 1):
+//     K1 = [c == 0],  K2 = [c == 1]
+//     g    = ~K1 & (sgn ^ K2)
+//     mag' = K1 ? mag : (~mag | g)
+//     sgn' = ~(mag ^ sgn ^ g)
+// Subtracting row r adds -r, whose masks are K1 = [r == 0], K2 = [r == -1]:
+// K1 is shared by both directions, only K2 differs (k2p / k2m below).
+// Columns j >= n are padding: they start as (1,0), i.e. the constant 1, and
+// every row holds 0 there, so they stay (1,0) and neither change the product
+// nor its sign.  The zero test of Sec. 3 ("mag == mask") then becomes
+// "every mag word is all ones".
+//
+// Gray order (Sec. 3, footnote on the reflected binary code): index i has
+// subset gray(i) = i ^ (i >> 1); step i flips row t = tz(i), and the row is
+// subtracted when bit t+1 of i is 1 (the bit is being cleared), added
+// otherwise.  The sign (-1)^{|S|} of Eq. (2) is (-1)^(i & 1) because each
+// step changes |S| by one.  The product of a subset sum with no zero entry is
+// (-1)^{popcount(sgn)} (Sec. 3, footnote on poppar).
+#pragma once
+#include <cstdint>
+
+namespace pf3 {
+
+constexpr int kMaxN = 64;
+
+template <int LUT>
+__device__ __forceinline__ uint32_t lop3(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("lop3.b32 %0, %1, %2, %3, %4;" : "=r"(d) : "r"(a), "r"(b), "r"(c), "n"(LUT));
+    return d;
+}
+
+// LUT immediates: F(0xF0, 0xCC, 0xAA) for inputs (a, b, c)
+constexpr int kLutG = 0x12;    // g    = ~b & (a ^ c)        a=sgn, b=K1, c=K2
+constexpr int kLutMag = 0xE3;  // mag' = b ? a : (~a | c)    a=mag, b=K1, c=g
+constexpr int kLutSgn = 0x69;  // sgn' = ~(a ^ b ^ c)        a=mag, b=sgn, c=g
+
+// add the per-column constant described by (k1, k2) to one word of the state
+__device__ __forceinline__ void add_word(uint32_t& m, uint32_t& s, uint32_t k1, uint32_t k2)
+{
+    const uint32_t g = lop3<kLutG>(s, k1, k2);
+    const uint32_t mn = lop3<kLutMag>(m, k1, g);
+    const uint32_t sn = lop3<kLutSgn>(m, s, g);
+    m = mn;
+    s = sn;
+}
+
+template <int W>
+struct State {
+    uint32_t m[W];
+    uint32_t s[W];
+};
+
+template <int W>
+__device__ __forceinline__ void add_masks(State<W>& st, const uint32_t (&k1)[W], const uint32_t (&k2)[W])
+{
+#pragma unroll
+    for (int w = 0; w < W; ++w) add_word(st.m[w], st.s[w], k1[w], k2[w]);
+}
+
+// Row tables in shared memory: for direction d (0 = add, 1 = subtract) and
+// row r, the W words of K1 followed by the W words of K2(d).
+template <int W>
+struct RowEntry {
+    uint32_t k1[W];
+    uint32_t k2[W];
+};
+
+template <int W>
+struct RowTable {
+    RowEntry<W> e[2][kMaxN];
+};
+
+// masks of one row from its packed mag/sgn words (K1 = ~mag, K2+ = mag & ~sgn,
+// K2- = mag & sgn); padding columns (mag = 0) get K1 = 1, K2 = 0.
+__device__ __forceinline__ void row_masks(uint32_t mag, uint32_t sgn, uint32_t& k1, uint32_t& k2p,
+                                          uint32_t& k2m)
+{
+    k1 = ~mag;
+    k2p = mag & ~sgn;
+    k2m = mag & sgn;
+}
+
+// initial state: the zero vector on the n real columns, the constant 1 on padding
+template <int W>
+__device__ __forceinline__ State<W> initial_state(int n)
+{
+    State<W> st;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        const int lo = 32 * w;
+        uint32_t real;
+        if (n >= lo + 32) real = 0xFFFFFFFFu;
+        else if (n <= lo) real = 0u;
+        else real = (1u << (n - lo)) - 1u;
+        st.m[w] = ~real;
+        st.s[w] = 0u;
+    }
+    return st;
+}
+
+template <int W>
+__device__ __forceinline__ void add_row(State<W>& st, const RowTable<W>& tab, int dir, int r)
+{
+    const RowEntry<W>& e = tab.e[dir][r];
+    uint32_t k1[W], k2[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        k1[w] = e.k1[w];
+        k2[w] = e.k2[w];
+    }
+    add_masks<W>(st, k1, k2);
+}
+
+// state for Gray index i: the subset sum of the rows in gray(i), from scratch
+// (Sec. 3.1: each block of consecutive Gray states starts from a direct jump)
+template <int W>
+__device__ __forceinline__ State<W> seed_state(const RowTable<W>& tab, int n, uint64_t i)
+{
+    State<W> st = initial_state<W>(n);
+    uint64_t g = i ^ (i >> 1);
+    while (g) {
+        const int r = __ffsll((long long)g) - 1;
+        add_row<W>(st, tab, 0, r);
+        g &= g - 1;
+    }
+    return st;
+}
+
+template <int W>
+__device__ __forceinline__ bool all_ones(const State<W>& st)
+{
+    bool ok = true;
+#pragma unroll
+    for (int w = 0; w < W; ++w) ok = ok && (st.m[w] == 0xFFFFFFFFu);
+    return ok;
+}
+
+// sign of a nonzero product times (-1)^{|S|}: 0 -> +1, 1 -> -1
+template <int W>
+__device__ __forceinline__ uint32_t term_parity(const State<W>& st, uint64_t i)
+{
+    uint32_t c = (uint32_t)i;
+#pragma unroll
+    for (int w = 0; w < W; ++w) c += __popc(st.s[w]);
+    return c & 1u;
+}
+
+struct Counts {
+    unsigned long long plus;
+    unsigned long long minus;
+};
+
+// Generic walk of Gray indices [first, last] (inclusive), every step looked up
+// in the row table.  Used for small n, ragged range ends and rare-path replays.
+template <int W>
+__device__ __noinline__ void walk_generic(const RowTable<W>& tab, int n, uint64_t first, uint64_t last,
+                                          Counts& c)
+{
+    State<W> st = seed_state<W>(tab, n, first);
+    uint64_t i = first;
+    for (;;) {
+        if (all_ones<W>(st)) {
+            if (term_parity<W>(st, i)) ++c.minus;
+            else ++c.plus;
+        }
+        if (i == last) break;
+        ++i;
+        const int t = __ffsll((long long)i) - 1;
+        const int dir = (int)((i >> (t + 1)) & 1u);
+        add_row<W>(st, tab, dir, t);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Grouped walk.  The Gray indices are cut into groups of 2^G consecutive
+// indices.  Only the first state of each group (the "base") is carried in
+// full (all W words of mag and sgn).  The other 2^G - 1 states of the group
+// differ from the base by a sum of rows 0..G-1 whose signs are fixed by the
+// index inside the group and the group's parity, so each is evaluated as a
+// "probe": base + C_j, computing only the low mag word (two LOP3) for the
+// zero test of Sec. 3.  A probe whose low 32 columns are all nonzero marks the
+// group; marked groups are replayed exactly (all words, sign from the
+// popcount of sgn) from the saved base.  The base moves to the next group by
+// one row-step with a combined constant (the group's net change of row G-1
+// plus the next group's first flip).
+//
+// Index facts used (reflected binary code, gray(i) = i ^ (i >> 1)):
+//  * for a base i = k * 2^G, the low G bits of gray(i) are (k & 1) << (G-1);
+//  * for i + j (0 < j < 2^G) they are gray(j) ^ ((k & 1) << (G-1)), so
+//    relative to the base, row r < G-1 is present (added) iff bit r of
+//    gray(j) is set, and row G-1 is present iff j >= 2^(G-1), added when k is
+//    even and subtracted when k is odd;
+//  * over one group the net change is row G-1 only (+ for even k, - for odd);
+//  * the flip entering group k+1 is row t = G + tz(k+1), subtracted iff bit
+//    t+1 of the index (k+1) * 2^G is set.
+// Groups are unrolled 2^(U-G) at a time ("block" of 2^U indices); inside a
+// block every row, sign and mask is a compile-time choice except the flip of
+// row U-1 in the middle of the block (sign = parity of the block index) and
+// the flip that enters the next block (row U + tz(B+1), from the row table).
+// ---------------------------------------------------------------------------
+
+__host__ __device__ constexpr int ctz_const(int x)
+{
+    return (x & 1) ? 0 : 1 + ctz_const(x >> 1);
+}
+
+__host__ __device__ constexpr int gray_const(int j)
+{
+    return j ^ (j >> 1);
+}
+
+template <int G>
+__host__ __device__ constexpr int probe_combos()
+{
+    return ((1 << (G - 1)) - 1) + 2 * (1 << (G - 1));
+}
+
+// probe j (1 <= j < 2^G) of a group with parity p -> its constant's slot
+template <int G>
+__host__ __device__ constexpr int probe_id(int j, int p)
+{
+    return j < (1 << (G - 1)) ? j - 1 : ((1 << (G - 1)) - 1) + 2 * (j - (1 << (G - 1))) + p;
+}
+
+// masks (K1 = [c == 0], K2 = [c == 1]) of the per-column constant
+// c = sum of rows in `plus` - sum of rows in `minus`
+template <int W>
+__device__ __forceinline__ void combo_masks(const RowTable<W>& tab, uint64_t plus, uint64_t minus,
+                                            uint32_t (&k1)[W], uint32_t (&k2)[W])
+{
+    State<W> c;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        c.m[w] = 0u;
+        c.s[w] = 0u;
+    }
+    while (plus) {
+        add_row<W>(c, tab, 0, __ffsll((long long)plus) - 1);
+        plus &= plus - 1;
+    }
+    while (minus) {
+        add_row<W>(c, tab, 1, __ffsll((long long)minus) - 1);
+        minus &= minus - 1;
+    }
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        k1[w] = ~c.m[w];
+        k2[w] = c.m[w] & ~c.s[w];
+    }
+}
+
+// Per-thread registers of the grouped walk: probe masks (low word only) and
+// the masks of the in-block group transitions (all words), slot
+// (t - G) * 2 + dir for row t and direction dir.
+template <int W, int G, int U>
+struct GroupRows {
+    static constexpr int kProbes = probe_combos<G>();
+    static constexpr int kTrans = 2 * (U - G);
+    uint32_t pk1[kProbes];
+    uint32_t pk2[kProbes];
+    uint32_t dk1[kTrans][W];
+    uint32_t dk2[kTrans][W];
+};
+
+template <int W, int G, int U>
+__device__ __forceinline__ void load_group_rows(GroupRows<W, G, U>& R, const RowTable<W>& tab)
+{
+    constexpr int H = 1 << (G - 1);
+#pragma unroll
+    for (int j = 1; j < (1 << G); ++j) {
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            if (j < H && p == 1) continue;
+            const uint64_t low = (uint64_t)(gray_const(j) & (H - 1));
+            uint64_t plus = low, minus = 0;
+            if (j >= H) {
+                if (p == 0) plus |= 1ull << (G - 1);
+                else minus |= 1ull << (G - 1);
+            }
+            uint32_t k1[W], k2[W];
+            combo_masks<W>(tab, plus, minus, k1, k2);
+            R.pk1[probe_id<G>(j, p)] = k1[0];
+            R.pk2[probe_id<G>(j, p)] = k2[0];
+        }
+    }
+#pragma unroll
+    for (int t = G; t < U; ++t) {
+#pragma unroll
+        for (int dir = 0; dir < 2; ++dir) {
+            // entering a group after an even one (t == G) the finished group
+            // added row G-1; after an odd one (t > G) it subtracted it
+            uint64_t plus = 0, minus = 0;
+            if (t == G) plus |= 1ull << (G - 1);
+            else minus |= 1ull << (G - 1);
+            if (dir == 0) plus |= 1ull << t;
+            else minus |= 1ull << t;
+            uint32_t k1[W], k2[W];
+            combo_masks<W>(tab, plus, minus, k1, k2);
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                R.dk1[(t - G) * 2 + dir][w] = k1[w];
+                R.dk2[(t - G) * 2 + dir][w] = k2[w];
+            }
+        }
+    }
+}
+
+// Exact terms of the group of 2^G indices starting at i0, from its base state.
+template <int W, int G>
+__device__ __noinline__ void replay_group(const RowTable<W>& tab, State<W> st, uint64_t i0, Counts& c)
+{
+    for (uint32_t j = 0; j < (1u << G); ++j) {
+        const uint64_t i = i0 + j;
+        if (j) {
+            const int t = __ffs((int)j) - 1;
+            const int dir = (int)((i >> (t + 1)) & 1u);
+            add_row<W>(st, tab, dir, t);
+        }
+        if (all_ones<W>(st)) {
+            if (term_parity<W>(st, i)) ++c.minus;
+            else ++c.plus;
+        }
+    }
+}
+
+// Per-warp queue of marked groups awaiting exact replay (shared memory).
+// Lanes push as they find marks; the whole warp drains the queue together,
+// one group per lane, so a rare replay does not stall 31 idle lanes.
+constexpr int kQueueCap = 64;
+
+template <int W>
+struct WarpQueue {
+    unsigned count;
+    unsigned pad;
+    unsigned long long i0[kQueueCap];
+    uint32_t m[kQueueCap][W];
+    uint32_t s[kQueueCap][W];
+};
+
+template <int W, int G>
+__device__ __noinline__ void queue_push(WarpQueue<W>& q, const RowTable<W>& tab, const State<W>& st, uint64_t i0,
+                                        Counts& c)
+{
+    const unsigned slot = atomicAdd(&q.count, 1u);
+    if (slot < (unsigned)kQueueCap) {
+        q.i0[slot] = i0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            q.m[slot][w] = st.m[w];
+            q.s[slot][w] = st.s[w];
+        }
+    } else {
+        replay_group<W, G>(tab, st, i0, c);  // queue full: replay in place
+    }
+}
+
+// all 32 lanes: replay the queued groups and empty the queue
+template <int W, int G>
+__device__ __forceinline__ void queue_drain(WarpQueue<W>& q, const RowTable<W>& tab, int lane, Counts& c)
+{
+    __syncwarp();
+    const unsigned cnt = *(volatile unsigned*)&q.count;
+    if (cnt == 0) return;
+    const unsigned lim = cnt < (unsigned)kQueueCap ? cnt : (unsigned)kQueueCap;
+    for (unsigned e = lane; e < lim; e += 32) {
+        State<W> st;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            st.m[w] = q.m[e][w];
+            st.s[w] = q.s[e][w];
+        }
+        replay_group<W, G>(tab, st, q.i0[e], c);
+    }
+    __syncwarp();
+    if (lane == 0) q.count = 0;
+    __syncwarp();
+}
+
+template <int W, int G, int U, int GI>
+struct GroupSteps {
+    static __device__ __forceinline__ void run(State<W>& st, const GroupRows<W, G, U>& R,
+                                               const uint32_t (&kmid1)[W], const uint32_t (&kmid2)[W],
+                                               uint64_t ibase, WarpQueue<W>& q, const RowTable<W>& tab,
+                                               Counts& c)
+    {
+        GroupSteps<W, G, U, GI - 1>::run(st, R, kmid1, kmid2, ibase, q, tab, c);
+        constexpr int g = GI - 1;            // group inside the block
+        constexpr int p = g & 1;             // its parity
+        bool hit = (st.m[0] == 0xFFFFFFFFu);
+#pragma unroll
+        for (int j = 1; j < (1 << G); ++j) {
+            const int id = probe_id<G>(j, p);
+            const uint32_t gq = lop3<kLutG>(st.s[0], R.pk1[id], R.pk2[id]);
+            const uint32_t mq = lop3<kLutMag>(st.m[0], R.pk1[id], gq);
+            hit |= (mq == 0xFFFFFFFFu);
+        }
+        if (hit) queue_push<W, G>(q, tab, st, ibase + ((uint64_t)g << G), c);
+        if (g + 1 < (1 << (U - G))) {
+            constexpr int t = G + ctz_const(g + 1);
+            constexpr int dir = ((g + 1) >> (t + 1 - G)) & 1;
+            if (t == U - 1) {
+                add_masks<W>(st, kmid1, kmid2);
+            } else {
+                constexpr int id = (t - G) * 2 + dir;
+                add_masks<W>(st, R.dk1[id], R.dk2[id]);
+            }
+        }
+    }
+};
+
+template <int W, int G, int U>
+struct GroupSteps<W, G, U, 0> {
+    static __device__ __forceinline__ void run(State<W>&, const GroupRows<W, G, U>&, const uint32_t (&)[W],
+                                               const uint32_t (&)[W], uint64_t, WarpQueue<W>&,
+                                               const RowTable<W>&, Counts&)
+    {
+    }
+};
+
+// Walk blocks [B0, B0 + len) of 2^U indices.  `trip` (>= len) must be the
+// same in all 32 lanes of the warp: lanes with len < trip idle through the
+// extra iterations so that the warp drains its queue together.
+template <int W, int G, int U>
+__device__ __forceinline__ void walk_groups(const RowTable<W>& tab, const GroupRows<W, G, U>& R, int n,
+                                            uint64_t B0, uint64_t len, uint64_t trip, WarpQueue<W>& q, int lane,
+                                            Counts& c)
+{
+    State<W> st = initial_state<W>(n);
+    if (len) st = seed_state<W>(tab, n, B0 << U);
+    constexpr int mid = (U - 1 - G) * 2;  // slot of the row U-1 transition
+    for (uint64_t it = 0; it < trip; ++it) {
+        if (it < len) {
+            const uint64_t B = B0 + it;
+            uint32_t kmid1[W], kmid2[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                kmid1[w] = (B & 1u) ? R.dk1[mid + 1][w] : R.dk1[mid][w];
+                kmid2[w] = (B & 1u) ? R.dk2[mid + 1][w] : R.dk2[mid][w];
+            }
+            GroupSteps<W, G, U, (1 << (U - G))>::run(st, R, kmid1, kmid2, B << U, q, tab, c);
+            if (it + 1 < len) {
+                // the block's last group (odd) subtracted row G-1 on the way;
+                // then the flip into block B+1
+                add_row<W>(st, tab, 1, G - 1);
+                const uint64_t nb = B + 1;
+                const int z = __ffsll((long long)nb) - 1;
+                add_row<W>(st, tab, (int)((nb >> (z + 1)) & 1u), U + z);
+            }
+        }
+        __syncwarp();
+        if (*(volatile unsigned*)&q.count >= 32u) queue_drain<W, G>(q, tab, lane, c);
+    }
+    queue_drain<W, G>(q, tab, lane, c);
+}
+
+// balanced split of `total` items over `parts`: part k gets [start, start+len)
+__device__ __forceinline__ void split_range(uint64_t total, uint64_t parts, uint64_t k, uint64_t& start,
+                                            uint64_t& len)
+{
+    const uint64_t q = total / parts, r = total % parts;
+    start = k * q + (k < r ? k : r);
+    len = q + (k < r ? 1 : 0);
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+
+// (-1)^n (plus - minus) mod 3, in {0,1,2} (Eq. (2) with the final cmod3 of Sec. 3)
+__device__ __forceinline__ uint32_t perm_from_counts(int n, unsigned long long plus, unsigned long long minus)
+{
+    int d = (int)(plus % 3ull) - (int)(minus % 3ull);
+    if (n & 1) d = -d;
+    return (uint32_t)((d + 3) % 3);
+}
+
+}  // namespace pf3
+
+namespace pf3 {
+
+// Pack row r of the n x n matrix A (entries {0,1,2}, 2 == -1) into bit planes
+// with one warp: lane l reads column l (and 32 + l).  Implements phi of Sec. 2
+// column by column.  `bad` is set in the lanes that saw an entry above 2.
+__device__ __forceinline__ void pack_row_warp(const uint8_t* A, int n, int r, int lane, uint32_t (&mag)[2],
+                                              uint32_t (&sgn)[2], bool& bad)
+{
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int col = 32 * h + lane;
+        uint32_t a = 0;
+        if (r < n && col < n) a = A[(size_t)r * n + col];
+        bad |= (a > 2u);
+        mag[h] = __ballot_sync(0xFFFFFFFFu, a == 1u || a == 2u);
+        sgn[h] = __ballot_sync(0xFFFFFFFFu, a == 2u);
+    }
+}
+
+// Build the row table of A with the warps [warp0, warp0 + nwarps) of the
+// calling group; every row r >= n is the identity (adds 0).
+template <int W>
+__device__ __forceinline__ bool build_row_table(RowTable<W>& tab, const uint8_t* A, int n, int warp, int nwarps,
+                                                int lane)
+{
+    bool bad = false;
+    for (int r = warp; r < kMaxN; r += nwarps) {
+        uint32_t mag[2], sgn[2];
+        pack_row_warp(A, n, r, lane, mag, sgn, bad);
+        if (lane < W) {
+            uint32_t k1, k2p, k2m;
+            row_masks(mag[lane], sgn[lane], k1, k2p, k2m);
+            tab.e[0][r].k1[lane] = k1;
+            tab.e[0][r].k2[lane] = k2p;
+            tab.e[1][r].k1[lane] = k1;
+            tab.e[1][r].k2[lane] = k2m;
+        }
+    }
+    return bad;
+}
+
+}  // namespace pf3

@@ -1,0 +1,53 @@
+// pf3_internal.h -- host-side declarations shared by the library's translation
+// units (not part of the public C ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace pf3 {
+
+// log2 of the unrolled Gray block (2^U consecutive indices per block) and of
+// the probe group (2^G indices per carried base state)
+constexpr int kBlockLog2 = 8;
+constexpr int kGroupLog2 = 4;
+constexpr int kSingleThreads = 256;
+
+// One range job for the single-matrix kernel; all indices are Gray indices.
+struct SingleArgs {
+    const uint8_t* A;        // device, n*n row-major {0,1,2}
+    int n;
+    int has_head;            // generic walk of [head_first, head_last]
+    int has_tail;            // generic walk of [tail_first, tail_last]
+    uint64_t head_first, head_last;
+    uint64_t tail_first, tail_last;
+    uint64_t mid_B0;         // aligned blocks [mid_B0, mid_B0 + mid_NB)
+    uint64_t mid_NB;
+    unsigned long long* partials;  // device scratch, 2 per CTA
+    unsigned int* ticket;          // device scratch, 0 between launches
+    unsigned int* err;             // device scratch, 0 between launches
+    unsigned long long* out;       // device: plus, minus, result (~0 on bad entry)
+};
+
+// split [first, last] into a ragged head, aligned middle blocks and a ragged tail
+void plan_range(int n, uint64_t first, uint64_t last, SingleArgs& a);
+
+// launch the single-matrix walk on `stream` with `grid` CTAs (grid <= max_grid)
+cudaError_t launch_single(const SingleArgs& a, int grid, cudaStream_t stream);
+
+// CTAs to launch for this plan given the device (one resident wave at most)
+int single_grid_for(const SingleArgs& a, int sm_count, int max_ctas_per_sm);
+
+// resident CTAs per SM of the single-matrix kernel for words-per-plane W
+int single_max_ctas_per_sm(int W);
+
+// device debug helpers
+cudaError_t launch_step_table(uint32_t* out, cudaStream_t stream);
+cudaError_t launch_pack(const uint8_t* A, int n, unsigned long long* out_mag, unsigned long long* out_sgn,
+                        unsigned int* err, cudaStream_t stream);
+
+// integer pipe microbenchmark
+cudaError_t launch_intpipe(int kind, int grid, int threads, int iters, uint32_t* sink,
+                           unsigned long long* cycles, cudaStream_t stream);
+
+}  // namespace pf3

@@ -1,0 +1,56 @@
+"""CPU-side checks of the C ABI: the library builds, loads, and exports every
+function include/perm_f3.h declares (no compute call: no GPU here)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+from conftest import ROOT
+
+HEADER = os.path.join(ROOT, "include", "perm_f3.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*([a-z][a-z0-9_]*)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for must in ("perm_f3", "perm_f3_batch", "perm_f3_range_counts", "perm_f3_counts",
+                 "perm_f3_range_counts_async", "perm_f3_batch_async", "pf3_strerror"):
+        assert must in names
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2407_20205_gb300 import build
+    return build.build()
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(line.split()[-1] for line in out.splitlines() if " T " in line)
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+
+
+def test_binding_loads_and_reports_errors(libpath):
+    from paper_2407_20205_gb300 import binding
+    assert binding.version().startswith("perm_f3")
+    assert binding.strerror(binding.PF3_EDOMAIN) == "matrix entry outside {0,1,2}"
+    assert set(binding.exported_symbols()) <= set(declared_functions())
+
+
+def test_no_oracle_in_product_path():
+    pkg = os.path.join(ROOT, "paper_2407_20205_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in src and "from oracle" not in src, f
+                assert "perm_f3_oracle" not in src, f

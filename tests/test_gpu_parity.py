@@ -1,0 +1,279 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Integer work, so every comparison is exact (tolerance 0): results in {0,1,2}
+and the (+1, -1) Ryser term counts.  The kernels walk ROW subsets (the
+paper's code, Sec. 3) while the oracle walks the COLUMN subsets of Eq. (2),
+so term counts are compared between A on the GPU and A^T in the oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from conftest import read_golden
+from paper_2407_20205_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pf3():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2407_20205_gb300 import binding
+    return binding
+
+
+def T(A):
+    return np.ascontiguousarray(np.asarray(A).T)
+
+
+# ------------------------------------------------------------ the row step
+
+def test_step_table_exhaustive(pf3):
+    """Every (state, constant, direction): psi(out) = psi(state) +- c (Thm 2.1)."""
+    tab = pf3.step_table()
+
+    def psi(m, s):
+        return 0 if m == 0 else (1 if s == 0 else 2)
+
+    for state in range(4):
+        m, s = state >> 1, state & 1
+        for c in range(3):
+            for d in range(2):
+                mo, so = tab[state, c, d]
+                want = (psi(m, s) + (c if d == 0 else -c)) % 3
+                assert psi(mo, so) == want, (state, c, d)
+                if c == 0 and m == 1:
+                    assert (mo, so) == (m, s)  # padding columns stay (1, 0)
+
+
+def test_step_table_matches_table1(pf3):
+    """Table 1: the determined outputs of addition are reproduced exactly; the
+    rows printed in red (sum 0) may use either zero representation."""
+    tab = pf3.step_table()
+    for row in read_golden("table1_addition.txt"):
+        a, b, m1, s1, m2, s2, mp, sp, free = map(int, row)
+        c = 0 if m2 == 0 else (1 if s2 == 0 else 2)
+        if m2 == 0 and s2 == 1:
+            continue  # the row constant is never the (0,1) zero (rows come from phi)
+        mo, so = tab[(m1 << 1) | s1, c, 0]
+        assert mo == mp
+        if not free:
+            assert so == sp
+
+
+def test_pack_worked_example(pf3):
+    row = read_golden("worked_example.txt")[0]
+    entries = [int(x) for x in row[0].split(",")]
+    n = len(entries)
+    mag_msb, sgn_msb = int(row[1], 16), int(row[2], 16)
+
+    def rev(x):
+        return int(format(x, f"0{n}b")[::-1], 2)
+
+    A = np.zeros((n, n), np.uint8)
+    A[0] = entries
+    mag, sgn = pf3.pack(A)
+    assert int(mag[0]) == rev(mag_msb) == 0xB
+    assert int(sgn[0]) == rev(sgn_msb) == 0x8
+
+
+# ------------------------------------------------------------ single matrix
+
+@pytest.mark.parametrize("n", list(range(1, 9)))
+def test_small_n_vs_bruteforce(pf3, oracle, n):
+    for A in inputs.uniform_matrices(1000 + n, n, 40):
+        assert pf3.perm_f3(A) == oracle.perm_bruteforce(A)
+
+
+@pytest.mark.parametrize("n", list(range(1, 25)))
+def test_counts_vs_oracle(pf3, oracle, n):
+    count = 6 if n <= 16 else (3 if n <= 21 else 1)
+    for A in inputs.uniform_matrices(2000 + n, n, count):
+        assert pf3.perm_f3_counts(A) == oracle.counts(T(A))
+        assert pf3.perm_f3(A) == oracle.perm_mod3(A)
+
+
+def test_config_n20_full(pf3, oracle):
+    A = inputs.uniform_matrix(inputs.SEED_N20, 20)
+    assert pf3.perm_f3_counts(A) == oracle.counts(T(A))
+    assert pf3.perm_f3(A) == oracle.perm_mod3(A)
+
+
+def _ranges(rng, n, k, maxlen):
+    top = (1 << n) - 1
+    out = [(0, min(top, 300)), (max(0, top - 300), top), (127, 129), (128, 255), (5, 5)]
+    for _ in range(k):
+        a = int(rng.integers(0, top + 1)) if n < 63 else int(rng.integers(0, 1 << 62)) << 2
+        a = min(a, top)
+        ln = int(rng.integers(0, maxlen))
+        out.append((a, min(top, a + ln)))
+    return [(a, b) for a, b in out if a <= b <= top]
+
+
+@pytest.mark.parametrize("n", [9, 14, 20, 31, 32, 33, 36, 40, 48, 63, 64])
+def test_range_counts_vs_oracle(pf3, oracle, n):
+    rng = np.random.default_rng(n)
+    A = inputs.uniform_matrix(3000 + n, n)
+    At = T(A)
+    for a, b in _ranges(rng, n, 12, 200000):
+        assert pf3.perm_f3_range_counts(A, a, b) == oracle.ryser_range(At, a, b), (a, b)
+
+
+def test_range_partition_adds_up(pf3):
+    """Sec. 3.1: disjoint blocks of Gray states add up to the whole sum."""
+    rng = np.random.default_rng(5)
+    for n in (18, 27, 34):
+        A = inputs.uniform_matrix(4000 + n, n)
+        whole = pf3.perm_f3_counts(A)
+        top = (1 << n) - 1
+        cuts = sorted(set(int(x) for x in rng.integers(1, top, 9)))
+        bounds = [0] + cuts + [top + 1]
+        tot = [0, 0]
+        for a, b in zip(bounds[:-1], bounds[1:]):
+            p, m = pf3.perm_f3_range_counts(A, a, b - 1)
+            tot[0] += p
+            tot[1] += m
+        assert tuple(tot) == whole
+
+
+# known answers at the benchmark sizes (n = 36, 40): closed forms and
+# oracle-sized factors; every one walks all 2^n Gray indices on the GPU
+
+@pytest.mark.parametrize("n", [33, 36, 40])
+def test_known_answers_large(pf3, oracle, n):
+    assert pf3.perm_f3(np.eye(n, dtype=np.uint8)) == 1
+    assert pf3.perm_f3(np.ones((n, n), np.uint8)) == math.factorial(n) % 3
+    st = inputs.Stream(77, n)
+    M = inputs.monomial(st, n)
+    expect = 1
+    for v in M[M != 0]:
+        expect = expect * int(v) % 3
+    assert pf3.perm_f3(M) == expect
+    # P1 * blockdiag(B1, B2) * P2 with two random blocks of about n/2
+    a = n // 2
+    B1 = inputs.uniform_matrix(5000 + n, a)
+    B2 = inputs.uniform_matrix(5001 + n, n - a)
+    P1, P2 = inputs.monomial(st, n), inputs.monomial(st, n)
+    X = inputs.f3_matmul(inputs.f3_matmul(P1, inputs.block_diag(B1, B2)), P2)
+    scale = 1
+    for v in list(P1[P1 != 0]) + list(P2[P2 != 0]):
+        scale = scale * int(v) % 3
+    expect = oracle.perm_mod3(B1) * oracle.perm_mod3(B2) * scale % 3
+    assert pf3.perm_f3(X) == expect
+
+
+@pytest.mark.parametrize("n", [36, 40])
+def test_config_sizes_invariances(pf3, n):
+    """The benchmark matrices at full size: properties that hold at any n."""
+    seed = inputs.SEED_N36 if n == 36 else inputs.SEED_N40
+    A = inputs.uniform_matrix(seed, n)
+    p = pf3.perm_f3(A)
+    assert p in (0, 1, 2)
+    assert pf3.perm_f3(T(A)) == p
+    rng = np.random.default_rng(n)
+    assert pf3.perm_f3(A[rng.permutation(n)][:, rng.permutation(n)].copy()) == p
+    S = A.copy()
+    S[3] = (2 * S[3].astype(np.int64) % 3).astype(np.uint8)
+    assert pf3.perm_f3(S) == (2 * p) % 3
+
+
+@pytest.mark.parametrize("n", [36, 48])
+def test_config_sizes_sampled_ranges(pf3, oracle, n):
+    """Full-size benchmark matrices: sampled Gray ranges, one by one."""
+    seed = inputs.SEED_N36 if n == 36 else inputs.SEED_N48
+    A = inputs.uniform_matrix(seed, n)
+    At = T(A)
+    rng = np.random.default_rng(1 + n)
+    top = (1 << n) - 1
+    for _ in range(8):
+        a = int(rng.integers(0, top - (1 << 18)))
+        b = a + int(rng.integers(1 << 16, 1 << 18))
+        assert pf3.perm_f3_range_counts(A, a, b) == oracle.ryser_range_par(At, a, b)
+
+
+def test_edge_cases(pf3):
+    assert pf3.perm_f3(np.zeros((0, 0), np.uint8)) == 1
+    assert pf3.perm_f3_counts(np.zeros((0, 0), np.uint8)) == (1, 0)
+    for v in (0, 1, 2):
+        assert pf3.perm_f3(np.array([[v]], np.uint8)) == v
+    with pytest.raises(pf3.PF3Error) as e:
+        pf3.perm_f3(np.array([[0, 3], [1, 1]], np.uint8))
+    assert e.value.code == pf3.PF3_EDOMAIN
+    with pytest.raises(pf3.PF3Error) as e:
+        pf3.perm_f3_range_counts(np.eye(4, dtype=np.uint8), 5, 16)
+    assert e.value.code == pf3.PF3_EINVAL
+    with pytest.raises(pf3.PF3Error):
+        pf3.perm_f3(np.zeros((65, 65), np.uint8))
+    # W = 2: a zero column makes every row-subset product 0; a zero row makes
+    # the terms of S and S + {row} cancel in pairs
+    Z = inputs.uniform_matrix(9, 40)
+    Z[:, 7] = 0
+    assert pf3.perm_f3(Z) == 0
+    assert pf3.perm_f3_counts(Z) == (0, 0)
+    Z = inputs.uniform_matrix(10, 35)
+    Z[4] = 0
+    p, m = pf3.perm_f3_counts(Z)
+    assert p == m and pf3.perm_f3(Z) == 0
+
+
+def test_device_pointer_entry(pf3, oracle):
+    import torch
+    A = inputs.uniform_matrix(11, 22)
+    dA = torch.from_numpy(A).cuda()
+    out = torch.zeros(3, dtype=torch.int64, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        pf3.perm_f3_range_counts_async(dA, 22, 0, (1 << 22) - 1, out, s)
+    s.synchronize()
+    p, m, r = [int(x) for x in out.cpu()]
+    assert (p, m) == oracle.counts(T(A))
+    assert r == oracle.perm_mod3(A)
+    bad = dA.clone()
+    bad[0, 0] = 7
+    with torch.cuda.stream(s):
+        pf3.perm_f3_range_counts_async(bad, 22, 0, (1 << 22) - 1, out, s)
+    s.synchronize()
+    assert int(out[2].cpu()) == -1  # UINT64_MAX flags the bad entry
+    # the scratch is clean again afterwards
+    with torch.cuda.stream(s):
+        pf3.perm_f3_range_counts_async(dA, 22, 0, (1 << 22) - 1, out, s)
+    s.synchronize()
+    assert int(out[2].cpu()) == r
+
+
+# ------------------------------------------------------------ batches
+
+def test_batch_uniform_n24_sample(pf3, oracle):
+    mats = list(inputs.uniform_matrices(inputs.SEED_BATCH24, 24, 24))
+    res, hist = pf3.perm_f3_batch(mats, with_hist=True)
+    want = oracle.perm_batch(mats)
+    assert list(res) == list(want)
+    assert list(hist) == [int((want == v).sum()) for v in range(3)]
+
+
+def test_batch_mixed_sizes(pf3, oracle):
+    rng = np.random.default_rng(8)
+    ns = [0, 1, 2, 3, 5, 7, 8, 9, 12, 16, 20, 22] + [int(x) for x in rng.integers(1, 23, 40)]
+    mats = [inputs.uniform_matrix(6000 + k, n) for k, n in enumerate(ns)]
+    res = pf3.perm_f3_batch(mats)
+    want = [1 if n == 0 else oracle.perm_mod3(M) for n, M in zip(ns, mats)]
+    assert list(res) == want
+
+
+def test_batch_single_vs_batch_identity(pf3):
+    """The same matrices alone and in a mixed batch (including split items)."""
+    ns = [36, 30, 29, 24, 13, 40]
+    mats = [inputs.uniform_matrix(7000 + k, n) for k, n in enumerate(ns)]
+    alone = [pf3.perm_f3(M) for M in mats]
+    assert list(pf3.perm_f3_batch(mats)) == alone
+
+
+def test_batch_bad_entry_and_empty(pf3):
+    mats = [np.eye(3, dtype=np.uint8), np.full((2, 2), 4, np.uint8)]
+    with pytest.raises(pf3.PF3Error) as e:
+        pf3.perm_f3_batch(mats)
+    assert e.value.code == pf3.PF3_EDOMAIN
+    assert len(pf3.perm_f3_batch([])) == 0
