@@ -218,6 +218,7 @@ def run_ours(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    tune = pf3.autotune()  # picks the kernel variants (untimed)
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             step()
@@ -308,7 +309,9 @@ def run_ours(args):
                            "l2": "flushed between steps (256 MB write)",
                            "results": {str(n): results[n] for n in SIZES},
                            "ms_per_launch": {str(n): float(np.mean(v)) for n, v in launch_ms.items()},
-                           "parallelism": f"range split x{world}" if world > 1 else "1 GPU"},
+                           "parallelism": f"range split x{world}" if world > 1 else "1 GPU",
+                           "variants": {"single": tune["single_variant"], "batch": tune["batch_variant"]},
+                           "autotune_ms": {"single": tune["single_ms"], "batch": tune["batch_ms"]}},
                 "clocks": clk, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": len(SIZES) * args.steps, "wall_s_timed": t_wall, "extra": extra}
         print(json.dumps(line), flush=True)

@@ -114,7 +114,9 @@ int pf3_step_table(uint32_t* out);
 int pf3_pack(const uint8_t* A, int n, uint64_t* mag, uint64_t* sgn);
 
 /* Integer-pipe microbenchmark (the roofline denominator of the walk).  kind:
- * 0 LOP3, 1 IMAD, 2 IADD, 3 LOP3+IMAD, 4 walk step (3 LOP3 + compare), 5 POPC.
+ * 0 LOP3, 1 IMAD, 2 IADD, 3 LOP3+IMAD, 4 full row step (3 LOP3 + compare),
+ * 5 POPC, 6 MAX(+IMAD), 7 2 LOP3 + MAX, 8 probe (2 LOP3 + compare),
+ * 9 row step + IMAD, 10 2 LOP3 + IADD.
  * Runs `ctas_per_sm` CTAs of `threads` threads per SM for `iters` rounds and
  * reports instructions per clock per SM (thread instructions, i.e. lanes),
  * thread instructions per second over the whole GPU, and the SM clock in MHz
@@ -124,6 +126,25 @@ int pf3_intpipe_bench(int kind, int ctas_per_sm, int threads, int iters, double*
 
 /* Device facts the roofline uses: SM count and the current device index. */
 int pf3_device_info(int* sm_count, int* device);
+
+/* ------------------------------------------------------------ tuning */
+
+/* Kernel variants (unrolled Gray block length, register budget).  which: 0 =
+ * single-matrix kernel, 1 = batch kernel.  W: words per plane (1 for n <= 32,
+ * 2 for n <= 64).  Results never depend on the variant, only speed does. */
+int pf3_variant_count(int which);
+int pf3_set_variant(int which, int W, int v);
+int pf3_get_variant(int which, int W);
+
+/* Batch work split: matrices with n > cutoff are cut into work items of
+ * 2^chunk_log2 Gray indices (Sec. 3.1 blocks); others are one item each. */
+int pf3_set_batch_split(int cutoff, int chunk_log2);
+
+/* Time every variant on the current device and keep the fastest per W.
+ * single_ms (pf3_variant_count(0) * 2 doubles) and batch_ms
+ * (pf3_variant_count(1) * 2 doubles) receive the timings, W = 1 first; either
+ * may be NULL.  Takes about a second. */
+int pf3_autotune(double* single_ms, double* batch_ms);
 
 #ifdef __cplusplus
 }

@@ -68,6 +68,11 @@ _lib_pack = _sig("pf3_pack", ctypes.c_int, [_u8p, ctypes.c_int, _u64p, _u64p])
 _lib_intpipe = _sig("pf3_intpipe_bench", ctypes.c_int,
                     [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp])
 _lib_devinfo = _sig("pf3_device_info", ctypes.c_int, [_ip, _ip])
+_lib_vcount = _sig("pf3_variant_count", ctypes.c_int, [ctypes.c_int])
+_lib_setv = _sig("pf3_set_variant", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int])
+_lib_getv = _sig("pf3_get_variant", ctypes.c_int, [ctypes.c_int, ctypes.c_int])
+_lib_split = _sig("pf3_set_batch_split", ctypes.c_int, [ctypes.c_int, ctypes.c_int])
+_lib_autotune = _sig("pf3_autotune", ctypes.c_int, [_dp, _dp])
 
 
 class PF3Error(RuntimeError):
@@ -221,8 +226,40 @@ def device_info() -> dict:
     return {"sm_count": sm.value, "device": dev.value}
 
 
+# ------------------------------------------------------------ tuning
+
+SINGLE, BATCH = 0, 1
+
+
+def variant_count(which: int) -> int:
+    return _check(_lib_vcount(which), "pf3_variant_count")
+
+
+def set_variant(which: int, W: int, v: int) -> None:
+    _check(_lib_setv(which, W, v), "pf3_set_variant")
+
+
+def get_variant(which: int, W: int) -> int:
+    return _check(_lib_getv(which, W), "pf3_get_variant")
+
+
+def set_batch_split(cutoff: int, chunk_log2: int) -> None:
+    _check(_lib_split(cutoff, chunk_log2), "pf3_set_batch_split")
+
+
+def autotune() -> dict:
+    ns, nb = variant_count(SINGLE), variant_count(BATCH)
+    a = (ctypes.c_double * (2 * ns))()
+    b = (ctypes.c_double * (2 * nb))()
+    _check(_lib_autotune(a, b), "pf3_autotune")
+    return {"single_ms": {1: list(a)[:ns], 2: list(a)[ns:]}, "batch_ms": {1: list(b)[:nb], 2: list(b)[nb:]},
+            "single_variant": {W: get_variant(SINGLE, W) for W in (1, 2)},
+            "batch_variant": {W: get_variant(BATCH, W) for W in (1, 2)}}
+
+
 def exported_symbols() -> list[str]:
     return [n for n in ("pf3_strerror", "pf3_version", "perm_f3", "perm_f3_counts",
                         "perm_f3_range_counts", "perm_f3_range_counts_async", "perm_f3_batch",
                         "perm_f3_batch_async", "pf3_step_table", "pf3_pack", "pf3_intpipe_bench",
-                        "pf3_device_info") if hasattr(_lib, n)]
+                        "pf3_device_info", "pf3_variant_count", "pf3_set_variant", "pf3_get_variant",
+                        "pf3_set_batch_split", "pf3_autotune") if hasattr(_lib, n)]

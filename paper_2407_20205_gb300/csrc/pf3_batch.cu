@@ -30,8 +30,8 @@ namespace {
 
 constexpr unsigned kBadBit = 0x80000000u;
 
-template <int W, int U>
-__global__ void __launch_bounds__(kBatchThreads) batch_kernel(BatchArgs a)
+template <int W, int U, int MINB>
+__global__ void __launch_bounds__(kBatchThreads, MINB) batch_kernel(BatchArgs a)
 {
     constexpr int G = kGroupLog2;
     __shared__ RowTable<W> tabs[kBatchThreads / 32];
@@ -112,38 +112,43 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(BatchArgs a)
 }
 
 template <int W>
-const void* batch_kernel_ptr()
+const void* batch_kernel_ptr(int v)
 {
-    return (const void*)batch_kernel<W, kBlockLog2>;
+    switch (v) {
+    case 0: return (const void*)batch_kernel<W, kBatchVariants[0].U, kBatchVariants[0].min_ctas>;
+    case 1: return (const void*)batch_kernel<W, kBatchVariants[1].U, kBatchVariants[1].min_ctas>;
+    case 2: return (const void*)batch_kernel<W, kBatchVariants[2].U, kBatchVariants[2].min_ctas>;
+    default: return (const void*)batch_kernel<W, kBatchVariants[3].U, kBatchVariants[3].min_ctas>;
+    }
 }
 
 }  // namespace
 
-int batch_max_ctas_per_sm(int W)
+int batch_max_ctas_per_sm(int W, int v)
 {
     int ctas = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, W == 1 ? batch_kernel_ptr<1>() : batch_kernel_ptr<2>(),
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, W == 1 ? batch_kernel_ptr<1>(v) : batch_kernel_ptr<2>(v),
                                                   kBatchThreads, 0);
     return ctas > 0 ? ctas : 1;
 }
 
-cudaError_t launch_batch(int W, const BatchArgs& a, int grid, cudaStream_t stream)
+cudaError_t launch_batch(int W, int v, const BatchArgs& a, int grid, cudaStream_t stream)
 {
-    if (W == 1) batch_kernel<1, kBlockLog2><<<grid, kBatchThreads, 0, stream>>>(a);
-    else batch_kernel<2, kBlockLog2><<<grid, kBatchThreads, 0, stream>>>(a);
-    return cudaGetLastError();
+    const void* fn = W == 1 ? batch_kernel_ptr<1>(v) : batch_kernel_ptr<2>(v);
+    void* args[] = {(void*)&a};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(kBatchThreads), args, 0, stream);
 }
 
 // ---------------------------------------------------------------- planning
 
 void plan_batch(const int32_t* ns, int64_t count, const BatchTuning& tune, BatchPlan& plan)
 {
+    const int Ucls[2] = {kBatchVariants[tune.variant[0]].U, kBatchVariants[tune.variant[1]].U};
     plan.items[0].clear();
     plan.items[1].clear();
     plan.split_items.clear();
     plan.num_split = 0;
     plan.total_bytes = 0;
-    constexpr int U = kBlockLog2;
     long long off = 0;
     for (int64_t k = 0; k < count; ++k) {
         const int n = ns[k];
@@ -154,6 +159,7 @@ void plan_batch(const int32_t* ns, int64_t count, const BatchTuning& tune, Batch
         it.n = n;
         it.split = -1;
         const int cls = n <= 32 ? 0 : 1;
+        const int U = Ucls[cls];
         off += (long long)n * n;
         if (n < U + 1) {
             it.B0 = 0;
@@ -267,12 +273,13 @@ int enqueue_batch(DeviceCtx* c, const BatchPlan& plan, const uint8_t* dAs, uint8
         a.items = (const WorkItem*)b.d_items + (cls == 1 ? 0 : n1);
         a.num_items = (unsigned)cnt;
         a.cursor = b.d_cursor + cls;
-        const int per_sm = c->batch_ctas[cls];
+        const int v = c->tune.variant[cls];
+        const int per_sm = batch_ctas(c, cls + 1, v);
         int grid = c->sm_count * per_sm;
         const size_t warps_needed = cnt;
         const size_t ctas_needed = (warps_needed + kBatchThreads / 32 - 1) / (kBatchThreads / 32);
         if ((size_t)grid > ctas_needed) grid = (int)ctas_needed;
-        if ((e = launch_batch(cls == 0 ? 1 : 2, a, grid, stream)) != cudaSuccess) return cuda_rc(e);
+        if ((e = launch_batch(cls == 0 ? 1 : 2, v, a, grid, stream)) != cudaSuccess) return cuda_rc(e);
     }
     return PF3_OK;
 }

@@ -37,6 +37,7 @@ struct BatchArgs {
 struct BatchTuning {
     int cutoff = 28;       // n above which a matrix is split over several items
     int chunk_log2 = 26;   // Gray indices per split item (log2)
+    int variant[2] = {0, 0};  // batch kernel variant for W = 1 and W = 2
 };
 
 struct BatchPlan {
@@ -47,7 +48,7 @@ struct BatchPlan {
 };
 
 void plan_batch(const int32_t* ns, int64_t count, const BatchTuning& tune, BatchPlan& plan);
-int batch_max_ctas_per_sm(int W);
-cudaError_t launch_batch(int W, const BatchArgs& a, int grid, cudaStream_t stream);
+int batch_max_ctas_per_sm(int W, int v);
+cudaError_t launch_batch(int W, int v, const BatchArgs& a, int grid, cudaStream_t stream);
 
 }  // namespace pf3

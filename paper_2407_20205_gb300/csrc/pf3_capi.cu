@@ -51,11 +51,15 @@ DeviceCtx* device_ctx(int* rc)
         return nullptr;
     }
     c->sm_count = prop.multiProcessorCount;
-    c->max_ctas[0] = single_max_ctas_per_sm(1);
-    c->max_ctas[1] = single_max_ctas_per_sm(2);
-    c->batch_ctas[0] = batch_max_ctas_per_sm(1);
-    c->batch_ctas[1] = batch_max_ctas_per_sm(2);
-    const int max_grid = c->sm_count * (c->max_ctas[0] > c->max_ctas[1] ? c->max_ctas[0] : c->max_ctas[1]);
+    int most = 1;
+    for (int W = 1; W <= 2; ++W)
+        for (int v = 0; v < kNumSingleVariants; ++v) {
+            c->single_ctas[W - 1][v] = single_max_ctas_per_sm(W, v);
+            if (c->single_ctas[W - 1][v] > most) most = c->single_ctas[W - 1][v];
+        }
+    for (int W = 1; W <= 2; ++W)
+        for (int v = 0; v < kNumBatchVariants; ++v) c->batch_ctas_cache[W - 1][v] = batch_max_ctas_per_sm(W, v);
+    const int max_grid = c->sm_count * most;
     c->max_grid = max_grid;
     bool ok = true;
     ok = ok && cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) == cudaSuccess;
@@ -77,6 +81,9 @@ DeviceCtx* device_ctx(int* rc)
     return c;
 }
 
+int single_ctas(DeviceCtx* c, int W, int v) { return c->single_ctas[W - 1][v]; }
+int batch_ctas(DeviceCtx* c, int W, int v) { return c->batch_ctas_cache[W - 1][v]; }
+
 int check_entries_host(const uint8_t* A, int n)
 {
     const size_t nn = (size_t)n * (size_t)n;
@@ -89,16 +96,18 @@ int check_entries_host(const uint8_t* A, int n)
 int enqueue_range(DeviceCtx* c, const uint8_t* dA, int n, uint64_t first, uint64_t last, unsigned long long* d_out,
                   cudaStream_t stream)
 {
+    const int W = n <= 32 ? 1 : 2;
+    const int v = c->single_variant[W - 1];
     SingleArgs a;
     std::memset(&a, 0, sizeof(a));
-    plan_range(n, first, last, a);
+    plan_range(n, first, last, kSingleVariants[v].U, a);
     a.A = dA;
     a.partials = c->d_partials;
     a.ticket = c->d_flags;
     a.err = c->d_flags + 1;
     a.out = d_out;
-    const int grid = single_grid_for(a, c->sm_count, c->max_ctas[n <= 32 ? 0 : 1]);
-    return cuda_rc(launch_single(a, grid, stream));
+    const int grid = single_grid_for(a, c->sm_count, single_ctas(c, W, v));
+    return cuda_rc(launch_single(a, v, grid, stream));
 }
 
 int valid_range(int n, uint64_t first, uint64_t last)

@@ -30,7 +30,9 @@ struct BatchScratch {
 struct DeviceCtx {
     int device = 0;
     int sm_count = 0;
-    int max_ctas[2] = {1, 1};  // single kernel, W = 1 / W = 2
+    int single_variant[2] = {0, 0};  // tuned single-kernel variant for W = 1 / W = 2
+    int single_ctas[2][8] = {};      // resident CTAs per SM by W and variant (0 = not queried)
+    int batch_ctas_cache[2][8] = {};
     int max_grid = 0;
     cudaStream_t stream = nullptr;
     // single-matrix scratch
@@ -43,13 +45,14 @@ struct DeviceCtx {
     BatchScratch batch;
     BatchTuning tune;
     BatchPlan last_plan;
-    int batch_ctas[2] = {1, 1};  // batch kernel, W = 1 / W = 2
     std::mutex mu;
 };
 
 int cuda_rc(cudaError_t e);
 DeviceCtx* device_ctx(int* rc);
 int check_entries_host(const uint8_t* A, int n);
+int single_ctas(DeviceCtx* c, int W, int v);
+int batch_ctas(DeviceCtx* c, int W, int v);
 struct BatchPlan;
 int enqueue_batch(DeviceCtx* c, const BatchPlan& plan, const uint8_t* dAs, uint8_t* d_results,
                   unsigned long long* d_hist, cudaStream_t stream);

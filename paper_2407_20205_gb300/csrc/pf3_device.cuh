@@ -354,10 +354,19 @@ struct WarpQueue {
     uint32_t s[kQueueCap][W];
 };
 
+// the base words travel by value (registers): a reference would force the
+// state into local memory at every call site of the walk's hot loop
 template <int W, int G>
-__device__ __noinline__ void queue_push(WarpQueue<W>& q, const RowTable<W>& tab, const State<W>& st, uint64_t i0,
-                                        Counts& c)
+__device__ __noinline__ void queue_push(WarpQueue<W>& q, const RowTable<W>& tab, uint32_t m0, uint32_t s0,
+                                        uint32_t m1, uint32_t s1, uint64_t i0, Counts* c)
 {
+    State<W> st;
+    st.m[0] = m0;
+    st.s[0] = s0;
+    if (W > 1) {
+        st.m[W - 1] = m1;
+        st.s[W - 1] = s1;
+    }
     const unsigned slot = atomicAdd(&q.count, 1u);
     if (slot < (unsigned)kQueueCap) {
         q.i0[slot] = i0;
@@ -367,7 +376,7 @@ __device__ __noinline__ void queue_push(WarpQueue<W>& q, const RowTable<W>& tab,
             q.s[slot][w] = st.s[w];
         }
     } else {
-        replay_group<W, G>(tab, st, i0, c);  // queue full: replay in place
+        replay_group<W, G>(tab, st, i0, *c);  // queue full: replay in place
     }
 }
 
@@ -411,7 +420,8 @@ struct GroupSteps {
             const uint32_t mq = lop3<kLutMag>(st.m[0], R.pk1[id], gq);
             hit |= (mq == 0xFFFFFFFFu);
         }
-        if (hit) queue_push<W, G>(q, tab, st, ibase + ((uint64_t)g << G), c);
+        if (hit)
+            queue_push<W, G>(q, tab, st.m[0], st.s[0], st.m[W - 1], st.s[W - 1], ibase + ((uint64_t)g << G), &c);
         if (g + 1 < (1 << (U - G))) {
             constexpr int t = G + ctz_const(g + 1);
             constexpr int dir = ((g + 1) >> (t + 1 - G)) & 1;

@@ -7,11 +7,20 @@
 
 namespace pf3 {
 
-// log2 of the unrolled Gray block (2^U consecutive indices per block) and of
-// the probe group (2^G indices per carried base state)
-constexpr int kBlockLog2 = 8;
+// log2 of the probe group (2^G Gray indices per carried base state)
 constexpr int kGroupLog2 = 4;
 constexpr int kSingleThreads = 256;
+
+// A compiled variant of a walk kernel: unrolled block of 2^U Gray indices and
+// the minimum resident CTAs per SM it was compiled for (its register budget).
+struct KernelVariant {
+    int U;
+    int min_ctas;
+};
+constexpr int kNumSingleVariants = 5;
+constexpr KernelVariant kSingleVariants[kNumSingleVariants] = {{8, 2}, {7, 2}, {8, 1}, {9, 1}, {9, 2}};
+constexpr int kNumBatchVariants = 4;
+constexpr KernelVariant kBatchVariants[kNumBatchVariants] = {{8, 4}, {7, 4}, {8, 2}, {9, 2}};
 
 // One range job for the single-matrix kernel; all indices are Gray indices.
 struct SingleArgs {
@@ -29,17 +38,18 @@ struct SingleArgs {
     unsigned long long* out;       // device: plus, minus, result (~0 on bad entry)
 };
 
-// split [first, last] into a ragged head, aligned middle blocks and a ragged tail
-void plan_range(int n, uint64_t first, uint64_t last, SingleArgs& a);
+// split [first, last] into a ragged head, aligned middle blocks of 2^U
+// indices and a ragged tail
+void plan_range(int n, uint64_t first, uint64_t last, int U, SingleArgs& a);
 
-// launch the single-matrix walk on `stream` with `grid` CTAs (grid <= max_grid)
-cudaError_t launch_single(const SingleArgs& a, int grid, cudaStream_t stream);
+// launch variant `v` of the single-matrix walk (W = 1 for n <= 32, else 2)
+cudaError_t launch_single(const SingleArgs& a, int v, int grid, cudaStream_t stream);
 
 // CTAs to launch for this plan given the device (one resident wave at most)
 int single_grid_for(const SingleArgs& a, int sm_count, int max_ctas_per_sm);
 
-// resident CTAs per SM of the single-matrix kernel for words-per-plane W
-int single_max_ctas_per_sm(int W);
+// resident CTAs per SM of variant v of the single-matrix kernel for W
+int single_max_ctas_per_sm(int W, int v);
 
 // device debug helpers
 cudaError_t launch_step_table(uint32_t* out, cudaStream_t stream);

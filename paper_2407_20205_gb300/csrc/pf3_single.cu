@@ -3,7 +3,7 @@
 //
 // Sec. 3.1 of the paper splits the 2^n Gray states into blocks of consecutive
 // states, each started by jumping to gray(start).  Here a block is 2^U
-// consecutive indices (U = kBlockLog2); thread k of the grid walks a
+// consecutive indices (U picked by the autotuner); thread k of the grid walks a
 // contiguous run of blocks, seeded once by a direct subset sum.  Each CTA
 // packs the matrix into a shared-memory row table itself (no separate pack
 // launch), the per-thread (+1, -1) term counts are reduced by warp shuffles
@@ -18,8 +18,8 @@ namespace pf3 {
 
 namespace {
 
-template <int W, int U>
-__global__ void __launch_bounds__(kSingleThreads) single_kernel(SingleArgs a)
+template <int W, int U, int MINB>
+__global__ void __launch_bounds__(kSingleThreads, MINB) single_kernel(SingleArgs a)
 {
     constexpr int G = kGroupLog2;
     __shared__ RowTable<W> tab;
@@ -145,21 +145,26 @@ __global__ void pack_kernel(const uint8_t* A, int n, unsigned long long* out_mag
 }
 
 template <int W>
-const void* single_kernel_ptr()
+const void* single_kernel_ptr(int v)
 {
-    return (const void*)single_kernel<W, kBlockLog2>;
+    switch (v) {
+    case 0: return (const void*)single_kernel<W, kSingleVariants[0].U, kSingleVariants[0].min_ctas>;
+    case 1: return (const void*)single_kernel<W, kSingleVariants[1].U, kSingleVariants[1].min_ctas>;
+    case 2: return (const void*)single_kernel<W, kSingleVariants[2].U, kSingleVariants[2].min_ctas>;
+    case 3: return (const void*)single_kernel<W, kSingleVariants[3].U, kSingleVariants[3].min_ctas>;
+    default: return (const void*)single_kernel<W, kSingleVariants[4].U, kSingleVariants[4].min_ctas>;
+    }
 }
 
 }  // namespace
 
-void plan_range(int n, uint64_t first, uint64_t last, SingleArgs& a)
+void plan_range(int n, uint64_t first, uint64_t last, int U, SingleArgs& a)
 {
     a.n = n;
     a.has_head = a.has_tail = 0;
     a.mid_B0 = a.mid_NB = 0;
     a.head_first = a.head_last = a.tail_first = a.tail_last = 0;
-    constexpr int U = kBlockLog2;
-    constexpr uint64_t bs = 1ull << U;
+    const uint64_t bs = 1ull << U;
     // blocks fully inside [first, last]
     const uint64_t B_begin = (first >> U) + ((first & (bs - 1)) ? 1 : 0);
     const uint64_t B_end = (last >> U) + (((last & (bs - 1)) == bs - 1) ? 1 : 0);
@@ -184,10 +189,10 @@ void plan_range(int n, uint64_t first, uint64_t last, SingleArgs& a)
     }
 }
 
-int single_max_ctas_per_sm(int W)
+int single_max_ctas_per_sm(int W, int v)
 {
     int ctas = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, W == 1 ? single_kernel_ptr<1>() : single_kernel_ptr<2>(),
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, W == 1 ? single_kernel_ptr<1>(v) : single_kernel_ptr<2>(v),
                                                   kSingleThreads, 0);
     return ctas > 0 ? ctas : 1;
 }
@@ -201,11 +206,11 @@ int single_grid_for(const SingleArgs& a, int sm_count, int max_ctas_per_sm)
     return (int)g;
 }
 
-cudaError_t launch_single(const SingleArgs& a, int grid, cudaStream_t stream)
+cudaError_t launch_single(const SingleArgs& a, int v, int grid, cudaStream_t stream)
 {
-    if (a.n <= 32) single_kernel<1, kBlockLog2><<<grid, kSingleThreads, 0, stream>>>(a);
-    else single_kernel<2, kBlockLog2><<<grid, kSingleThreads, 0, stream>>>(a);
-    return cudaGetLastError();
+    const void* fn = a.n <= 32 ? single_kernel_ptr<1>(v) : single_kernel_ptr<2>(v);
+    void* args[] = {(void*)&a};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(kSingleThreads), args, 0, stream);
 }
 
 cudaError_t launch_step_table(uint32_t* out, cudaStream_t stream)

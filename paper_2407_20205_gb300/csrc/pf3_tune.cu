@@ -1,0 +1,190 @@
+// pf3_tune.cu -- variant selection and the autotuner.
+//
+// Each walk kernel is compiled in a few variants (unrolled block length 2^U,
+// register budget).  The autotuner times every variant of the single-matrix
+// kernel and of the batch kernel on the current device, separately for one
+// and two words per plane, and keeps the fastest; the batch split length is
+// chosen on a mixed-size sample.  Sample matrices come from a fixed xorshift
+// stream (uniform entries in {0,1,2}).
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "perm_f3.h"
+#include "pf3_batch.h"
+#include "pf3_context.h"
+#include "pf3_internal.h"
+
+namespace pf3 {
+
+int enqueue_range(DeviceCtx* c, const uint8_t* dA, int n, uint64_t first, uint64_t last, unsigned long long* d_out,
+                  cudaStream_t stream);
+
+namespace {
+
+void sample_matrix(uint8_t* A, int n, uint64_t seed)
+{
+    uint64_t x = seed * 0x9E3779B97F4A7C15ull + 1;
+    for (int k = 0; k < n * n;) {
+        x ^= x << 13;
+        x ^= x >> 7;
+        x ^= x << 17;
+        const unsigned v = (unsigned)(x >> 60) & 3u;
+        if (v < 3) A[k++] = (uint8_t)v;
+    }
+}
+
+// average milliseconds of `reps` launches of fn after one warm-up
+template <class F>
+float time_ms(cudaStream_t s, int reps, F fn)
+{
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    fn();
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps; ++r) fn();
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ms / reps;
+}
+
+}  // namespace
+
+}  // namespace pf3
+
+using namespace pf3;
+
+extern "C" {
+
+int pf3_variant_count(int which)
+{
+    if (which == 0) return kNumSingleVariants;
+    if (which == 1) return kNumBatchVariants;
+    return PF3_EINVAL;
+}
+
+int pf3_set_variant(int which, int W, int v)
+{
+    if (W < 1 || W > 2 || v < 0) return PF3_EINVAL;
+    if ((which == 0 && v >= kNumSingleVariants) || (which == 1 && v >= kNumBatchVariants) || which < 0 ||
+        which > 1)
+        return PF3_EINVAL;
+    int rc;
+    DeviceCtx* c = device_ctx(&rc);
+    if (!c) return rc;
+    std::lock_guard<std::mutex> g(c->mu);
+    if (which == 0) c->single_variant[W - 1] = v;
+    else c->tune.variant[W - 1] = v;
+    return PF3_OK;
+}
+
+int pf3_get_variant(int which, int W)
+{
+    if (W < 1 || W > 2 || which < 0 || which > 1) return PF3_EINVAL;
+    int rc;
+    DeviceCtx* c = device_ctx(&rc);
+    if (!c) return rc;
+    return which == 0 ? c->single_variant[W - 1] : c->tune.variant[W - 1];
+}
+
+int pf3_set_batch_split(int cutoff, int chunk_log2)
+{
+    if (cutoff < 0 || cutoff > PF3_MAX_N || chunk_log2 < 12 || chunk_log2 > 62) return PF3_EINVAL;
+    int rc;
+    DeviceCtx* c = device_ctx(&rc);
+    if (!c) return rc;
+    std::lock_guard<std::mutex> g(c->mu);
+    c->tune.cutoff = cutoff;
+    c->tune.chunk_log2 = chunk_log2;
+    return PF3_OK;
+}
+
+int pf3_autotune(double* single_ms, double* batch_ms)
+{
+    int rc;
+    DeviceCtx* c = device_ctx(&rc);
+    if (!c) return rc;
+    std::lock_guard<std::mutex> g(c->mu);
+    cudaStream_t s = c->stream;
+    // ---- single-matrix kernel: n = 32 over 2^31 indices, n = 40 over 2^34
+    const int nW[2] = {32, 40};
+    const int lgW[2] = {31, 34};
+    uint8_t* dA = nullptr;
+    unsigned long long* dout = nullptr;
+    cudaError_t e = cudaMalloc(&dA, kMaxNN);
+    if (e == cudaSuccess) e = cudaMalloc(&dout, 4 * sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        cudaFree(dA);
+        return cuda_rc(e);
+    }
+    std::vector<uint8_t> hA(kMaxNN);
+    for (int W = 1; W <= 2; ++W) {
+        const int n = nW[W - 1];
+        sample_matrix(hA.data(), n, 1000 + n);
+        cudaMemcpy(dA, hA.data(), (size_t)n * n, cudaMemcpyHostToDevice);
+        float best = 1e30f;
+        int bestv = 0;
+        for (int v = 0; v < kNumSingleVariants; ++v) {
+            c->single_variant[W - 1] = v;
+            const float ms = time_ms(s, 2, [&] {
+                enqueue_range(c, dA, n, 0, (1ull << lgW[W - 1]) - 1, dout, s);
+            });
+            if (single_ms) single_ms[(W - 1) * kNumSingleVariants + v] = ms;
+            if (ms < best) {
+                best = ms;
+                bestv = v;
+            }
+        }
+        c->single_variant[W - 1] = bestv;
+    }
+    // ---- batch kernel: 3072 whole matrices of n = 24 (W = 1); 20 matrices of
+    // n = 33 cut into split items (W = 2)
+    const int bn[2] = {24, 33};
+    const int bcount[2] = {3072, 20};
+    for (int W = 1; W <= 2; ++W) {
+        const int n = bn[W - 1], cnt = bcount[W - 1];
+        std::vector<int32_t> ns(cnt, n);
+        std::vector<uint8_t> hAs((size_t)cnt * n * n);
+        for (int k = 0; k < cnt; ++k) sample_matrix(hAs.data() + (size_t)k * n * n, n, 77 + k);
+        uint8_t* dAs = nullptr;
+        uint8_t* dres = nullptr;
+        e = cudaMalloc(&dAs, hAs.size());
+        if (e == cudaSuccess) e = cudaMalloc(&dres, cnt);
+        if (e != cudaSuccess) break;
+        cudaMemcpy(dAs, hAs.data(), hAs.size(), cudaMemcpyHostToDevice);
+        const BatchTuning keep = c->tune;
+        if (W == 1) c->tune.cutoff = PF3_MAX_N;  // whole matrices per warp
+        else c->tune.cutoff = 28, c->tune.chunk_log2 = 26;
+        float best = 1e30f;
+        int bestv = 0;
+        for (int v = 0; v < kNumBatchVariants; ++v) {
+            c->tune.variant[W - 1] = v;
+            BatchPlan plan;
+            plan_batch(ns.data(), cnt, c->tune, plan);
+            const float ms = time_ms(s, 1, [&] { enqueue_batch(c, plan, dAs, dres, nullptr, s); });
+            if (batch_ms) batch_ms[(W - 1) * kNumBatchVariants + v] = ms;
+            if (ms < best) {
+                best = ms;
+                bestv = v;
+            }
+        }
+        c->tune = keep;
+        c->tune.variant[W - 1] = bestv;
+        cudaFree(dAs);
+        cudaFree(dres);
+    }
+    cudaFree(dA);
+    cudaFree(dout);
+    e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return cuda_rc(e);
+}
+
+}  // extern "C"

@@ -1,0 +1,37 @@
+"""One small, self-contained launch for profilers.
+
+    python -m paper_2407_20205_gb300.profile_case --kind single --n 36
+    python -m paper_2407_20205_gb300.profile_case --kind batch --n 24 --count 2000
+
+single: perm of the seeded uniform n x n matrix (one launch of the walk);
+batch: one batch call over `count` seeded uniform n x n matrices.
+"""
+from __future__ import annotations
+
+import argparse
+
+import numpy as np
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--kind", default="single", choices=["single", "batch"])
+    ap.add_argument("--n", type=int, default=36)
+    ap.add_argument("--count", type=int, default=2000)
+    ap.add_argument("--seed", type=int, default=None)
+    a = ap.parse_args()
+    from . import binding, inputs
+    if a.kind == "single":
+        seed = a.seed if a.seed is not None else a.n
+        r = binding.perm_f3(inputs.uniform_matrix(seed, a.n))
+        print(f"perm mod 3 = {r}")
+    else:
+        seed = a.seed if a.seed is not None else inputs.SEED_BATCH24
+        A = inputs.uniform_matrices(seed, a.n, a.count)
+        res, hist = binding.perm_f3_batch(flat=A.reshape(-1), ns=np.full(a.count, a.n, np.int32),
+                                          with_hist=True)
+        print(f"hist = {list(hist)}")
+
+
+if __name__ == "__main__":
+    main()

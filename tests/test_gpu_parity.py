@@ -277,3 +277,53 @@ def test_batch_bad_entry_and_empty(pf3):
         pf3.perm_f3_batch(mats)
     assert e.value.code == pf3.PF3_EDOMAIN
     assert len(pf3.perm_f3_batch([])) == 0
+
+
+# ------------------------------------------------------------ every variant
+
+def test_every_single_variant(pf3, oracle):
+    """Each compiled variant of the walk gives the same exact counts."""
+    keep = {W: pf3.get_variant(pf3.SINGLE, W) for W in (1, 2)}
+    try:
+        cases = [(n, inputs.uniform_matrix(8000 + n, n)) for n in (9, 17, 24, 33, 37)]
+        rng = np.random.default_rng(3)
+        for v in range(pf3.variant_count(pf3.SINGLE)):
+            for W in (1, 2):
+                pf3.set_variant(pf3.SINGLE, W, v)
+            for n, A in cases:
+                if n <= 24:
+                    assert pf3.perm_f3_counts(A) == oracle.counts(T(A)), (v, n)
+                top = (1 << n) - 1
+                a = int(rng.integers(0, max(1, top - 65537)))
+                b = min(top, a + 65537)
+                assert pf3.perm_f3_range_counts(A, a, b) == oracle.ryser_range(T(A), a, b), (v, n)
+    finally:
+        for W in (1, 2):
+            pf3.set_variant(pf3.SINGLE, W, keep[W])
+
+
+def test_every_batch_variant(pf3, oracle):
+    keep = {W: pf3.get_variant(pf3.BATCH, W) for W in (1, 2)}
+    try:
+        ns = [5, 9, 13, 17, 20, 22, 3, 12]
+        mats = [inputs.uniform_matrix(8100 + k, n) for k, n in enumerate(ns)]
+        want = [oracle.perm_mod3(M) for M in mats]
+        big = [inputs.uniform_matrix(8200 + k, n) for k, n in enumerate((33, 35))]
+        pf3.set_batch_split(28, 20)  # split the W = 2 matrices into many items
+        want_big = [pf3.perm_f3(M) for M in big]
+        for v in range(pf3.variant_count(pf3.BATCH)):
+            for W in (1, 2):
+                pf3.set_variant(pf3.BATCH, W, v)
+            assert list(pf3.perm_f3_batch(mats)) == want, v
+            assert list(pf3.perm_f3_batch(big)) == want_big, v
+    finally:
+        pf3.set_batch_split(28, 26)
+        for W in (1, 2):
+            pf3.set_variant(pf3.BATCH, W, keep[W])
+
+
+def test_autotune_keeps_results(pf3, oracle):
+    rep = pf3.autotune()
+    assert all(t > 0 for t in rep["single_ms"][1] + rep["single_ms"][2])
+    A = inputs.uniform_matrix(8300, 21)
+    assert pf3.perm_f3_counts(A) == oracle.counts(T(A))
