@@ -52,6 +52,7 @@ extern "C" {
 #define PF3_ETIMEDOUT (-5)   /* perm_f3_wait: the deadline passed */
 #define PF3_ECANCELED (-6)   /* the job or context was cancelled */
 #define PF3_EBUSY (-7)       /* perm_f3_submit: the request queue is full */
+#define PF3_ETOOBIG (-8)     /* more CTAs requested than the fixed no-allocation scratch holds */
 
 #define PF3_MAX_N 64
 
@@ -84,6 +85,26 @@ int perm_f3_range_counts(const uint8_t* A, int n, uint64_t first, uint64_t last,
  * stream: a cudaStream_t. */
 int perm_f3_range_counts_async(const uint8_t* dA, int n, uint64_t first, uint64_t last, uint64_t* d_out,
                                void* stream);
+
+/* No-allocation form of perm_f3_range_counts_async, for callers that must not
+ * let a library allocate device memory -- for instance a process whose memory
+ * manager reserves the whole GPU up front and forbids allocations it did not
+ * make, or a latency-sensitive caller that cannot afford cudaMalloc/cudaFree,
+ * which may synchronise the whole device.  (The paper has no counterpart: this
+ * is a library-interface concern.)  Same arguments, results and stream
+ * ordering as perm_f3_range_counts_async; the caller owns dA and d_out.  The
+ * kernel's scratch lives in a fixed device array inside the library
+ * (PF3_NOALLOC_MAX_CTAS * 16 + 256 bytes, held by every GPU that loads the
+ * library until the process exits), so this entry point never calls
+ * cudaMalloc or cudaFree.  ctas: CTAs to launch, 0 = one resident wave;
+ * values above PF3_NOALLOC_MAX_CTAS are rejected with PF3_ETOOBIG.  The first
+ * call on each device looks up the array's device address and the kernel's
+ * occupancy; make that first call before any stream capture.  All calls on a
+ * device share the array (each call clears its flags first): calls that
+ * overlap on the GPU race and must be ordered by the caller. */
+#define PF3_NOALLOC_MAX_CTAS 1024
+int perm_f3_range_counts_noalloc(const uint8_t* dA, int n, uint64_t first, uint64_t last, uint64_t* d_out,
+                                 int ctas, void* stream);
 
 /* ------------------------------------------------------------ batches */
 

@@ -42,7 +42,9 @@ PF3_ENOMEM = -4
 PF3_ETIMEDOUT = -5
 PF3_ECANCELED = -6
 PF3_EBUSY = -7
+PF3_ETOOBIG = -8
 MAX_N = 64
+NOALLOC_MAX_CTAS = 1024
 
 
 def _sig(name, restype, argtypes):
@@ -60,6 +62,8 @@ _lib_range = _sig("perm_f3_range_counts", ctypes.c_int,
                   [_u8p, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, _u64p, _u64p])
 _lib_range_async = _sig("perm_f3_range_counts_async", ctypes.c_int,
                         [_vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, _vp, _vp])
+_lib_range_noalloc = _sig("perm_f3_range_counts_noalloc", ctypes.c_int,
+                          [_vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, _vp, ctypes.c_int, _vp])
 _lib_batch = _sig("perm_f3_batch", ctypes.c_int, [_u8p, _i32p, ctypes.c_int64, _u8p, _u64p])
 _lib_batch_async = _sig("perm_f3_batch_async", ctypes.c_int,
                         [_vp, _i32p, ctypes.c_int64, _vp, _vp, _vp])
@@ -157,6 +161,17 @@ def perm_f3_range_counts_async(dA, n: int, first: int, last: int, d_out, stream=
     """Device form: dA (n*n bytes) and d_out (3 x uint64) on the device."""
     _check(_lib_range_async(_dev_ptr(dA), n, first, last, _dev_ptr(d_out), _stream_ptr(stream)),
            "perm_f3_range_counts_async")
+
+
+def perm_f3_range_counts_noalloc(dA, n: int, first: int, last: int, d_out, ctas: int = 0,
+                                 stream=None) -> None:
+    """Same as perm_f3_range_counts_async, but the library allocates nothing:
+    its scratch is a fixed array inside the library (for callers whose memory
+    manager forbids foreign device allocations, or that cannot afford the
+    device-wide synchronisation cudaMalloc may cause).  The first call on a
+    device looks up that array; calls that overlap on the GPU race."""
+    _check(_lib_range_noalloc(_dev_ptr(dA), n, first, last, _dev_ptr(d_out), ctas, _stream_ptr(stream)),
+           "perm_f3_range_counts_noalloc")
 
 
 # ------------------------------------------------------------ batches
@@ -262,4 +277,5 @@ def exported_symbols() -> list[str]:
                         "perm_f3_range_counts", "perm_f3_range_counts_async", "perm_f3_batch",
                         "perm_f3_batch_async", "pf3_step_table", "pf3_pack", "pf3_intpipe_bench",
                         "pf3_device_info", "pf3_variant_count", "pf3_set_variant", "pf3_get_variant",
-                        "pf3_set_batch_split", "pf3_autotune") if hasattr(_lib, n)]
+                        "pf3_set_batch_split", "pf3_autotune", "perm_f3_range_counts_noalloc")
+            if hasattr(_lib, n)]

@@ -160,6 +160,7 @@ const char* pf3_strerror(int code)
     case PF3_ETIMEDOUT: return "timed out";
     case PF3_ECANCELED: return "cancelled";
     case PF3_EBUSY: return "queue full";
+    case PF3_ETOOBIG: return "more CTAs requested than the no-allocation scratch holds";
     default: return "unknown error";
     }
 }
