@@ -106,6 +106,23 @@ int perm_f3_range_counts_async(const uint8_t* dA, int n, uint64_t first, uint64_
 int perm_f3_range_counts_noalloc(const uint8_t* dA, int n, uint64_t first, uint64_t last, uint64_t* d_out,
                                  int ctas, void* stream);
 
+/* Long walks in bounded launches (Sec. 3.1's split of the Gray range into
+ * jobs, here consecutive launches of at most 2^chunk_log2 indices each).
+ * After every launch the exact counts and the next Gray index are written to
+ * checkpoint_path (temporary file + rename; NULL = no checkpoint).  If the
+ * file already holds a checkpoint of the same matrix, the walk resumes from
+ * it; one of another matrix is refused (PF3_EINVAL).  Stops between launches
+ * when max_seconds (> 0) of wall time have passed (PF3_ETIMEDOUT) or when
+ * pf3_longrun_cancel(1) was called (PF3_ECANCELED); the counts so far are
+ * returned and saved either way.  *finished = 1 once the whole range is done;
+ * *next_index is the first index not yet walked (0 when finished). */
+int pf3_longrun(const uint8_t* A, int n, int chunk_log2, const char* checkpoint_path, double max_seconds,
+                uint64_t* plus, uint64_t* minus, uint64_t* next_index, int* finished);
+
+/* Set (1) or clear (0) the flag that makes pf3_longrun stop at its next
+ * launch boundary; callable from any thread. */
+void pf3_longrun_cancel(int on);
+
 /* ------------------------------------------------------------ batches */
 
 /* perm mod 3 of `count` matrices in one call.  As: host, the matrices back to
@@ -121,6 +138,63 @@ int perm_f3_batch(const uint8_t* As, const int32_t* ns, int64_t count, uint8_t* 
  * `stream`; an entry outside {0,1,2} gives result 255 for that matrix. */
 int perm_f3_batch_async(const uint8_t* dAs, const int32_t* ns, int64_t count, uint8_t* d_results,
                         uint64_t* d_hist, void* stream);
+
+/* ------------------------------------------------------------ serving */
+
+/* A request loop for streams of permanents (the Monte Carlo use of Sec. 4):
+ * requests are admitted as device slots free up, each request's Gray range is
+ * cut into work items of 2^chunk_log2 indices (Sec. 3.1 blocks), and every
+ * launch of the batch kernel runs items of many requests under a work budget
+ * (a reserved share for the oldest request, then least remaining work first).
+ * Matrices and partial counts stay on the device until a request finishes.
+ * A context is driven by its own host thread; all calls are thread-safe. */
+typedef struct pf3_config {
+    int32_t max_jobs;        /* device slots (requests resident at once); default 4096 */
+    int32_t queue_depth;     /* requests waiting for a slot before PF3_EBUSY; default 2^20 */
+    int32_t chunk_log2;      /* Gray indices per work item (log2); default 20 */
+    int32_t launch_items;    /* work items per launch at most; default 16384 */
+    int32_t max_admit;       /* requests admitted per launch at most; default 1024 */
+    int32_t pad;
+    uint64_t launch_budget;  /* Gray indices per launch (soft cap); default 2^33 */
+} pf3_config;
+
+typedef struct pf3_ctx pf3_ctx;
+
+/* Fill cfg with the defaults above. */
+void pf3_config_default(pf3_config* cfg);
+
+/* Create a serving context on the current device (cfg NULL = defaults). */
+int pf3_create(pf3_ctx** ctx, const pf3_config* cfg);
+
+/* Finish admitted requests, cancel queued ones (PF3_ECANCELED), free all.
+ * No other thread may use ctx during or after this call. */
+void pf3_destroy(pf3_ctx* ctx);
+
+/* Cancel every request still waiting for a slot (they report PF3_ECANCELED);
+ * admitted requests run to completion.  Returns how many were cancelled. */
+int pf3_cancel_queued(pf3_ctx* ctx);
+
+/* Queue perm(A) mod 3; A (host, n*n bytes) is copied.  Returns a ticket >= 0,
+ * or PF3_EBUSY when queue_depth requests are already waiting, PF3_EDOMAIN /
+ * PF3_EINVAL on bad input. */
+int64_t perm_f3_submit(pf3_ctx* ctx, const uint8_t* A, int n);
+
+/* PF3_OK with *result set, PF3_PENDING, or the request's error code. */
+int perm_f3_poll(pf3_ctx* ctx, int64_t ticket, uint8_t* result);
+
+/* Block until the request finishes or timeout_us passes (negative: no
+ * limit).  PF3_OK, PF3_ETIMEDOUT or the request's error code. */
+int perm_f3_wait(pf3_ctx* ctx, int64_t ticket, uint8_t* result, int64_t timeout_us);
+
+/* Host steady-clock times (ns) of submission and of the result becoming
+ * visible; PF3_PENDING while unfinished. */
+int pf3_job_times(pf3_ctx* ctx, int64_t ticket, uint64_t* submit_ns, uint64_t* done_ns);
+
+/* Launches issued, work items run and requests finished so far. */
+int pf3_serve_stats(pf3_ctx* ctx, uint64_t* launches, uint64_t* items, uint64_t* jobs_done);
+
+/* The steady clock the serving times use (ns). */
+uint64_t pf3_now_ns(void);
 
 /* ------------------------------------------------------------ diagnostics */
 

@@ -206,6 +206,132 @@ def perm_f3_batch_async(dAs, ns, d_results, d_hist, stream=None) -> None:
            "perm_f3_batch_async")
 
 
+# ------------------------------------------------------------ long runs
+
+_lib_longrun = _sig("pf3_longrun", ctypes.c_int,
+                    [_u8p, ctypes.c_int, ctypes.c_int, ctypes.c_char_p, ctypes.c_double, _u64p, _u64p, _u64p, _ip])
+_lib_longrun_cancel = _sig("pf3_longrun_cancel", None, [ctypes.c_int])
+
+
+def longrun(A, chunk_log2: int = 42, checkpoint: str | None = None, max_seconds: float = 0.0) -> dict:
+    """Walk all 2^n Gray indices in launches of 2^chunk_log2, checkpointing
+    after each; returns counts, progress and the return code (PF3_OK,
+    PF3_ETIMEDOUT or PF3_ECANCELED leave a resumable checkpoint)."""
+    a, p, n = _square(A)
+    P, M, nxt, fin = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_int()
+    rc = _lib_longrun(p, n, chunk_log2, checkpoint.encode() if checkpoint else None, max_seconds,
+                      ctypes.byref(P), ctypes.byref(M), ctypes.byref(nxt), ctypes.byref(fin))
+    if rc < 0 and rc not in (PF3_ETIMEDOUT, PF3_ECANCELED):
+        raise PF3Error(rc, "pf3_longrun")
+    res = {"rc": rc, "plus": P.value, "minus": M.value, "next_index": nxt.value, "finished": bool(fin.value)}
+    if fin.value:
+        d = P.value - M.value
+        res["perm"] = (-d if n & 1 else d) % 3
+    return res
+
+
+def longrun_cancel(on: bool = True) -> None:
+    _lib_longrun_cancel(1 if on else 0)
+
+
+# ------------------------------------------------------------ serving
+
+class PF3Config(ctypes.Structure):
+    _fields_ = [("max_jobs", ctypes.c_int32), ("queue_depth", ctypes.c_int32), ("chunk_log2", ctypes.c_int32),
+                ("launch_items", ctypes.c_int32), ("max_admit", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("launch_budget", ctypes.c_uint64)]
+
+
+_lib_cfg_default = _sig("pf3_config_default", None, [ctypes.POINTER(PF3Config)])
+_lib_create = _sig("pf3_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(PF3Config)])
+_lib_destroy = _sig("pf3_destroy", None, [ctypes.c_void_p])
+_lib_submit = _sig("perm_f3_submit", ctypes.c_int64, [ctypes.c_void_p, _u8p, ctypes.c_int])
+_lib_poll = _sig("perm_f3_poll", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, _u8p])
+_lib_wait = _sig("perm_f3_wait", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, _u8p, ctypes.c_int64])
+_lib_times = _sig("pf3_job_times", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, _u64p, _u64p])
+_lib_stats = _sig("pf3_serve_stats", ctypes.c_int, [ctypes.c_void_p, _u64p, _u64p, _u64p])
+_lib_now = _sig("pf3_now_ns", ctypes.c_uint64, [])
+_lib_cancel = _sig("pf3_cancel_queued", ctypes.c_int, [ctypes.c_void_p])
+
+
+def config_default() -> PF3Config:
+    c = PF3Config()
+    _lib_cfg_default(ctypes.byref(c))
+    return c
+
+
+def now_ns() -> int:
+    return int(_lib_now())
+
+
+class ServeContext:
+    """pf3_create / perm_f3_submit / perm_f3_poll / perm_f3_wait."""
+
+    def __init__(self, **overrides):
+        cfg = config_default()
+        for k, v in overrides.items():
+            setattr(cfg, k, v)
+        self._h = ctypes.c_void_p()
+        _check(_lib_create(ctypes.byref(self._h), ctypes.byref(cfg)), "pf3_create")
+        self.config = cfg
+
+    def close(self):
+        if self._h:
+            _lib_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, A) -> int:
+        a, p, n = _square(A)
+        return _check(int(_lib_submit(self._h, p if n else None, n)), "perm_f3_submit")
+
+    def try_submit(self, A) -> int:
+        """Like submit, but returns the negative code (e.g. PF3_EBUSY) instead of raising."""
+        a, p, n = _square(A)
+        return int(_lib_submit(self._h, p if n else None, n))
+
+    def poll(self, ticket: int):
+        r = ctypes.c_uint8()
+        rc = _lib_poll(self._h, ticket, ctypes.byref(r))
+        if rc == PF3_PENDING:
+            return None
+        _check(rc, "perm_f3_poll")
+        return int(r.value)
+
+    def wait(self, ticket: int, timeout_us: int = -1) -> int:
+        r = ctypes.c_uint8()
+        _check(_lib_wait(self._h, ticket, ctypes.byref(r), timeout_us), "perm_f3_wait")
+        return int(r.value)
+
+    def wait_code(self, ticket: int, timeout_us: int = -1) -> int:
+        r = ctypes.c_uint8()
+        return int(_lib_wait(self._h, ticket, ctypes.byref(r), timeout_us))
+
+    def times(self, ticket: int) -> tuple[int, int]:
+        a, b = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(_lib_times(self._h, ticket, ctypes.byref(a), ctypes.byref(b)), "pf3_job_times")
+        return int(a.value), int(b.value)
+
+    def cancel_queued(self) -> int:
+        return _check(_lib_cancel(self._h), "pf3_cancel_queued", "pf3_longrun", "pf3_longrun_cancel")
+
+    def stats(self) -> dict:
+        a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(_lib_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "pf3_serve_stats")
+        return {"launches": a.value, "items": b.value, "jobs_done": c.value}
+
+
 # ------------------------------------------------------------ diagnostics
 
 def step_table() -> np.ndarray:
@@ -277,5 +403,8 @@ def exported_symbols() -> list[str]:
                         "perm_f3_range_counts", "perm_f3_range_counts_async", "perm_f3_batch",
                         "perm_f3_batch_async", "pf3_step_table", "pf3_pack", "pf3_intpipe_bench",
                         "pf3_device_info", "pf3_variant_count", "pf3_set_variant", "pf3_get_variant",
-                        "pf3_set_batch_split", "pf3_autotune", "perm_f3_range_counts_noalloc")
+                        "pf3_set_batch_split", "pf3_autotune", "perm_f3_range_counts_noalloc",
+                        "pf3_config_default", "pf3_create", "pf3_destroy", "perm_f3_submit", "perm_f3_poll",
+                        "perm_f3_wait", "pf3_job_times", "pf3_serve_stats", "pf3_now_ns",
+                        "pf3_cancel_queued", "pf3_longrun", "pf3_longrun_cancel")
             if hasattr(_lib, n)]

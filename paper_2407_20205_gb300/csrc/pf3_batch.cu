@@ -111,6 +111,24 @@ __global__ void __launch_bounds__(kBatchThreads, MINB) batch_kernel(BatchArgs a)
     }
 }
 
+// one CTA per admitted job: matrix into its slot, counters reset
+__global__ void slot_init_kernel(const SlotInit* inits, int count, const uint8_t* staging, uint8_t* mats,
+                                 int slot_bytes, unsigned long long* acc, unsigned* left, uint8_t* results)
+{
+    const int k = blockIdx.x;
+    if (k >= count) return;
+    const SlotInit in = inits[k];
+    const int nn = in.n * in.n;
+    uint8_t* dst = mats + (size_t)in.slot * slot_bytes;
+    for (int i = threadIdx.x; i < nn; i += blockDim.x) dst[i] = staging[in.src + i];
+    if (threadIdx.x == 0) {
+        acc[2 * in.slot] = 0ull;
+        acc[2 * in.slot + 1] = 0ull;
+        left[in.slot] = in.items;
+        results[in.slot] = 0xFEu;
+    }
+}
+
 template <int W>
 const void* batch_kernel_ptr(int v)
 {
@@ -137,6 +155,15 @@ cudaError_t launch_batch(int W, int v, const BatchArgs& a, int grid, cudaStream_
     const void* fn = W == 1 ? batch_kernel_ptr<1>(v) : batch_kernel_ptr<2>(v);
     void* args[] = {(void*)&a};
     return cudaLaunchKernel(fn, dim3(grid), dim3(kBatchThreads), args, 0, stream);
+}
+
+cudaError_t launch_slot_init(const SlotInit* inits, int count, const uint8_t* staging, uint8_t* mats,
+                             int slot_bytes, unsigned long long* acc, unsigned* left, uint8_t* results,
+                             cudaStream_t stream)
+{
+    if (count <= 0) return cudaSuccess;
+    slot_init_kernel<<<count, 128, 0, stream>>>(inits, count, staging, mats, slot_bytes, acc, left, results);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- planning
@@ -174,7 +201,8 @@ void plan_batch(const int32_t* ns, int64_t count, const BatchTuning& tune, Batch
             plan.items[cls].push_back(it);
             continue;
         }
-        const int cl = std::max(tune.chunk_log2, U + 5);
+        // at most 2^20 items per matrix keeps the item table small for n near 64
+        const int cl = std::max(std::max(tune.chunk_log2, U + 5), n - 20);
         const uint64_t per = 1ull << (cl - U);
         const uint64_t nitems = (NB + per - 1) / per;
         it.split = plan.num_split++;

@@ -47,7 +47,20 @@ struct BatchPlan {
     long long total_bytes = 0;
 };
 
+// A job admitted into a serving slot: copy its matrix from the staging buffer
+// into the slot and reset the slot's counters.
+struct SlotInit {
+    long long src;        // byte offset in the device staging buffer
+    int slot;
+    int n;
+    unsigned items;       // work items the job will run in total
+    unsigned pad;
+};
+
 void plan_batch(const int32_t* ns, int64_t count, const BatchTuning& tune, BatchPlan& plan);
+cudaError_t launch_slot_init(const SlotInit* inits, int count, const uint8_t* staging, uint8_t* mats,
+                             int slot_bytes, unsigned long long* acc, unsigned* left, uint8_t* results,
+                             cudaStream_t stream);
 int batch_max_ctas_per_sm(int W, int v);
 cudaError_t launch_batch(int W, int v, const BatchArgs& a, int grid, cudaStream_t stream);
 

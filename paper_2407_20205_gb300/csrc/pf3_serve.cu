@@ -1,0 +1,567 @@
+// pf3_serve.cu -- continuous batching of permanent requests.
+//
+// The Monte Carlo studies of Sec. 4 consume perm(A) for a stream of random
+// matrices; this runtime serves such a stream as requests arrive.  A
+// scheduler thread owns a pool of device slots: every admitted job keeps its
+// matrix, its two partial counts and its count of outstanding work items on
+// the device until its last item finishes.  Each job's Gray range is cut into
+// work items of 2^chunk_log2 indices (Sec. 3.1's blocks of consecutive Gray
+// states).  Every launch of the persistent batch kernel takes items from many
+// jobs at once under a work budget: first a reserved share for the oldest
+// unfinished job (so large jobs always progress), then the jobs with the
+// least remaining work.  Up to two launches are in flight; new requests are
+// admitted into free slots between launches, so work that arrives while
+// other jobs run overlaps with them on the GPU.  Nothing on the device waits
+// on the host: completion is observed with CUDA events, and the host polls
+// them with short sleeps.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "perm_f3.h"
+#include "pf3_batch.h"
+#include "pf3_context.h"
+#include "pf3_internal.h"
+
+using namespace pf3;
+
+namespace {
+
+constexpr int kSlotBytes = kMaxNN;
+constexpr unsigned char kPending = 0xFEu;
+
+uint64_t now_ns()
+{
+    return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+               std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+enum JobState : int { kQueued = 0, kAdmitted = 1, kDone = 2, kFailed = 3 };
+
+struct Job {
+    int n = 0;
+    int state = kQueued;
+    int slot = -1;
+    int result = -1;
+    int error = 0;
+    std::vector<uint8_t> A;
+    uint64_t nb = 0;          // Gray blocks of 2^U (0: one generic item)
+    uint64_t per_item = 0;    // blocks per work item
+    uint64_t cursor = 0;      // next block to issue
+    uint64_t items_total = 0;
+    uint64_t items_issued = 0;
+    uint64_t t_submit = 0;
+    uint64_t t_done = 0;
+    uint64_t remaining_work() const { return nb ? (nb - cursor) : (items_issued ? 0 : 1); }
+};
+
+struct Launch {
+    int buf = 0;
+    std::vector<int64_t> finishing;
+};
+
+}  // namespace
+
+struct pf3_ctx {
+    pf3_config cfg;
+    int device = 0;
+    DeviceCtx* dc = nullptr;
+    int U[2] = {8, 8};
+    int variant[2] = {0, 0};
+    int grid[2] = {1, 1};
+    cudaStream_t streams[2] = {nullptr, nullptr};  // launches alternate between them
+    cudaEvent_t kdone[2] = {nullptr, nullptr};     // after each launch's kernels
+    // device state
+    uint8_t* d_mats = nullptr;
+    unsigned long long* d_acc = nullptr;
+    unsigned* d_left = nullptr;
+    uint8_t* d_results = nullptr;
+    uint8_t* d_stage[2] = {nullptr, nullptr};
+    void* d_table[2] = {nullptr, nullptr};    // SlotInit[max_admit] then WorkItem[max_items]
+    unsigned* d_cursor = nullptr;             // 2 buffers x 2 classes
+    // pinned host mirrors
+    uint8_t* h_stage[2] = {nullptr, nullptr};
+    void* h_table[2] = {nullptr, nullptr};
+    uint8_t* h_results[2] = {nullptr, nullptr};
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    // host bookkeeping
+    std::mutex mu;
+    std::condition_variable cv_done;
+    std::condition_variable cv_work;
+    std::vector<Job> jobs;
+    std::deque<int64_t> pending;
+    std::vector<int64_t> active;  // admitted, items left to issue
+    std::vector<int> free_slots;
+    std::deque<Launch> inflight;
+    std::thread th;
+    bool stop = false;
+    int fatal = 0;
+    uint64_t launches = 0, items = 0, done = 0;
+};
+
+namespace {
+
+size_t table_bytes(const pf3_config& c)
+{
+    return (size_t)c.max_admit * sizeof(SlotInit) + (size_t)c.launch_items * sizeof(WorkItem);
+}
+
+void fail_all(pf3_ctx* x, int code)
+{
+    // caller holds x->mu
+    x->fatal = code;
+    for (auto& j : x->jobs)
+        if (j.state == kQueued || j.state == kAdmitted) {
+            j.state = kFailed;
+            j.error = code;
+            j.t_done = now_ns();
+        }
+    x->pending.clear();
+    x->active.clear();
+    x->cv_done.notify_all();
+}
+
+// harvest the oldest in-flight launch once its event has completed
+bool harvest(pf3_ctx* x, bool block)
+{
+    if (x->inflight.empty()) return false;
+    Launch& L = x->inflight.front();
+    cudaError_t e = block ? cudaEventSynchronize(x->ev[L.buf]) : cudaEventQuery(x->ev[L.buf]);
+    if (e == cudaErrorNotReady) return false;
+    std::lock_guard<std::mutex> g(x->mu);
+    if (e != cudaSuccess) {
+        fail_all(x, PF3_ECUDA);
+        x->inflight.pop_front();
+        return true;
+    }
+    const uint64_t t = now_ns();
+    for (int64_t tk : L.finishing) {
+        Job& j = x->jobs[tk];
+        const unsigned char r = x->h_results[L.buf][j.slot];
+        if (r < 3) {
+            j.result = r;
+            j.state = kDone;
+        } else {
+            j.state = kFailed;
+            j.error = (r == 255) ? PF3_EDOMAIN : PF3_ECUDA;
+        }
+        j.t_done = t;
+        x->free_slots.push_back(j.slot);
+        ++x->done;
+    }
+    x->inflight.pop_front();
+    x->cv_done.notify_all();
+    return true;
+}
+
+// build and enqueue one launch; returns false when there was nothing to do
+bool launch_once(pf3_ctx* x)
+{
+    int buf;
+    {
+        std::lock_guard<std::mutex> g(x->mu);
+        buf = (int)(x->launches & 1);
+    }
+    SlotInit* inits = (SlotInit*)x->h_table[buf];
+    WorkItem* items = (WorkItem*)((char*)x->h_table[buf] + (size_t)x->cfg.max_admit * sizeof(SlotInit));
+    std::vector<WorkItem> cls_items[2];
+    Launch L;
+    L.buf = buf;
+    int n_inits = 0;
+    size_t stage_off = 0;
+    {
+        std::lock_guard<std::mutex> g(x->mu);
+        if (x->fatal) return false;
+        // admit queued jobs into free slots
+        while (!x->pending.empty() && !x->free_slots.empty() && n_inits < x->cfg.max_admit) {
+            const int64_t tk = x->pending.front();
+            Job& j = x->jobs[tk];
+            const size_t nn = (size_t)j.n * j.n;
+            if (stage_off + nn > (size_t)x->cfg.max_admit * kSlotBytes) break;
+            x->pending.pop_front();
+            j.slot = x->free_slots.back();
+            x->free_slots.pop_back();
+            std::memcpy(x->h_stage[buf] + stage_off, j.A.data(), nn);
+            std::vector<uint8_t>().swap(j.A);
+            const int cls = j.n <= 32 ? 0 : 1;
+            const int U = x->U[cls];
+            if (j.n <= U) {
+                j.nb = 0;
+                j.items_total = 1;
+            } else {
+                j.nb = (j.n == 64) ? (1ull << (64 - U)) : (1ull << (j.n - U));
+                // items per job stay below 2^30 (the device counter's range)
+                const int cl = std::max(std::max(x->cfg.chunk_log2, U + 5), j.n - 30);
+                j.per_item = (cl - U >= 63) ? j.nb : (1ull << (cl - U));
+                if (j.per_item > j.nb) j.per_item = j.nb;
+                j.items_total = (j.nb + j.per_item - 1) / j.per_item;
+            }
+            j.state = kAdmitted;
+            inits[n_inits].src = (long long)stage_off;
+            inits[n_inits].slot = j.slot;
+            inits[n_inits].n = j.n;
+            inits[n_inits].items = (unsigned)j.items_total;
+            ++n_inits;
+            stage_off += nn;
+            x->active.push_back(tk);
+        }
+        // choose items: the oldest job's reserved share, then least remaining work
+        uint64_t budget = x->cfg.launch_budget;
+        int n_items = 0;
+        auto issue = [&](int64_t tk, uint64_t share) {
+            Job& j = x->jobs[tk];
+            while (j.items_issued < j.items_total && n_items < x->cfg.launch_items) {
+                WorkItem it;
+                std::memset(&it, 0, sizeof(it));
+                it.offset = (long long)j.slot * kSlotBytes;
+                it.mat = j.slot;
+                it.n = j.n;
+                it.split = j.slot;
+                uint64_t cost;
+                if (j.nb == 0) {
+                    it.B0 = 0;
+                    it.NB = 0;
+                    cost = 1ull << j.n;
+                } else {
+                    it.B0 = j.cursor;
+                    it.NB = std::min<unsigned long long>(j.per_item, j.nb - j.cursor);
+                    cost = (uint64_t)it.NB << x->U[j.n <= 32 ? 0 : 1];
+                }
+                if (cost > share && n_items > 0) break;  // the first item always goes
+                share = cost > share ? 0 : share - cost;
+                budget = cost > budget ? 0 : budget - cost;
+                j.cursor += it.NB;
+                ++j.items_issued;
+                cls_items[j.n <= 32 ? 0 : 1].push_back(it);
+                ++n_items;
+                if (j.items_issued == j.items_total) L.finishing.push_back(tk);
+                if (share == 0) break;
+            }
+        };
+        if (!x->active.empty()) {
+            issue(x->active.front(), budget / 4);
+            std::vector<int64_t> order;
+            for (int64_t tk : x->active)
+                if (x->jobs[tk].items_issued < x->jobs[tk].items_total) order.push_back(tk);
+            std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+                const Job& ja = x->jobs[a];
+                const Job& jb = x->jobs[b];
+                const uint64_t ra = ja.nb ? (ja.nb - ja.cursor) << x->U[ja.n <= 32 ? 0 : 1] : (1ull << ja.n);
+                const uint64_t rb = jb.nb ? (jb.nb - jb.cursor) << x->U[jb.n <= 32 ? 0 : 1] : (1ull << jb.n);
+                return ra < rb;
+            });
+            for (int64_t tk : order) {
+                if (budget == 0 || n_items >= x->cfg.launch_items) break;
+                issue(tk, budget);
+            }
+            // drop fully issued jobs from the active list
+            std::vector<int64_t> keep;
+            for (int64_t tk : x->active)
+                if (x->jobs[tk].items_issued < x->jobs[tk].items_total) keep.push_back(tk);
+            x->active.swap(keep);
+        }
+        x->items += (uint64_t)(cls_items[0].size() + cls_items[1].size());
+    }
+    const size_t n1 = cls_items[1].size(), n0 = cls_items[0].size();
+    if (n_inits == 0 && n0 + n1 == 0) return false;
+    // items: class W = 2 first, then W = 1
+    if (n1) std::memcpy(items, cls_items[1].data(), n1 * sizeof(WorkItem));
+    if (n0) std::memcpy(items + n1, cls_items[0].data(), n0 * sizeof(WorkItem));
+    cudaStream_t s = x->streams[buf];
+    const size_t inits_bytes = (size_t)x->cfg.max_admit * sizeof(SlotInit);
+    cudaError_t e = cudaSuccess;
+    if (stage_off) e = cudaMemcpyAsync(x->d_stage[buf], x->h_stage[buf], stage_off, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && n_inits)
+        e = cudaMemcpyAsync(x->d_table[buf], x->h_table[buf], (size_t)n_inits * sizeof(SlotInit),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && n0 + n1)
+        e = cudaMemcpyAsync((char*)x->d_table[buf] + inits_bytes, items, (n0 + n1) * sizeof(WorkItem),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = launch_slot_init((const SlotInit*)x->d_table[buf], n_inits, x->d_stage[buf], x->d_mats, kSlotBytes,
+                             x->d_acc, x->d_left, x->d_results, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(x->d_cursor + 2 * buf, 0, 2 * sizeof(unsigned), s);
+    const WorkItem* d_items = (const WorkItem*)((char*)x->d_table[buf] + inits_bytes);
+    for (int cls = 1; cls >= 0 && e == cudaSuccess; --cls) {
+        const size_t cnt = cls == 1 ? n1 : n0;
+        if (!cnt) continue;
+        BatchArgs a;
+        a.As = x->d_mats;
+        a.items = d_items + (cls == 1 ? 0 : n1);
+        a.num_items = (unsigned)cnt;
+        a.cursor = x->d_cursor + 2 * buf + cls;
+        a.acc = x->d_acc;
+        a.left = x->d_left;
+        a.results = x->d_results;
+        a.hist = nullptr;
+        const size_t ctas_needed = (cnt + kBatchThreads / 32 - 1) / (kBatchThreads / 32);
+        int grid = x->grid[cls];
+        if ((size_t)grid > ctas_needed) grid = (int)ctas_needed;
+        e = launch_batch(cls + 1, x->variant[cls], a, grid, s);
+    }
+    // the previous launch (other stream) may still run items of jobs that
+    // finish here: copy results only after its kernels are done too
+    if (e == cudaSuccess) e = cudaEventRecord(x->kdone[buf], s);
+    if (e == cudaSuccess && x->launches > 0) e = cudaStreamWaitEvent(s, x->kdone[buf ^ 1], 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(x->h_results[buf], x->d_results, (size_t)x->cfg.max_jobs, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaEventRecord(x->ev[buf], s);
+    if (e != cudaSuccess) {
+        std::lock_guard<std::mutex> g(x->mu);
+        fail_all(x, cuda_rc(e));
+        return false;
+    }
+    x->inflight.push_back(std::move(L));
+    std::lock_guard<std::mutex> g(x->mu);
+    ++x->launches;
+    return true;
+}
+
+void scheduler(pf3_ctx* x)
+{
+    cudaSetDevice(x->device);
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lk(x->mu);
+            if (x->stop && x->pending.empty() && x->active.empty() && x->inflight.empty()) break;
+            if (x->fatal && x->inflight.empty()) {
+                if (x->stop) break;
+                x->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+                continue;
+            }
+            const bool can_launch = !x->active.empty() || (!x->pending.empty() && !x->free_slots.empty());
+            if (!can_launch && x->inflight.empty()) {
+                x->cv_work.wait_for(lk, std::chrono::milliseconds(2));
+                continue;
+            }
+        }
+        // retire finished launches without blocking
+        while (harvest(x, false)) {
+        }
+        if ((int)x->inflight.size() >= 2) {
+            // both buffers busy: wait briefly for the oldest
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
+            continue;
+        }
+        if (!launch_once(x)) {
+            if (!x->inflight.empty()) std::this_thread::sleep_for(std::chrono::microseconds(20));
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+void pf3_config_default(pf3_config* cfg)
+{
+    if (!cfg) return;
+    cfg->max_jobs = 4096;
+    cfg->queue_depth = 1 << 20;
+    cfg->chunk_log2 = 20;
+    cfg->launch_items = 16384;
+    cfg->max_admit = 1024;
+    cfg->launch_budget = 1ull << 33;
+}
+
+int pf3_create(pf3_ctx** out, const pf3_config* cfg_in)
+{
+    if (!out) return PF3_EINVAL;
+    pf3_config cfg;
+    pf3_config_default(&cfg);
+    if (cfg_in) cfg = *cfg_in;
+    if (cfg.max_jobs < 1 || cfg.max_jobs > (1 << 20) || cfg.queue_depth < 1 || cfg.chunk_log2 < 13 ||
+        cfg.chunk_log2 > 62 || cfg.launch_items < 1 || cfg.max_admit < 1 || cfg.launch_budget < 1)
+        return PF3_EINVAL;
+    int rc;
+    DeviceCtx* dc = device_ctx(&rc);
+    if (!dc) return rc;
+    pf3_ctx* x = new pf3_ctx();
+    x->cfg = cfg;
+    x->dc = dc;
+    x->device = dc->device;
+    for (int cls = 0; cls < 2; ++cls) {
+        x->variant[cls] = dc->tune.variant[cls];
+        x->U[cls] = kBatchVariants[x->variant[cls]].U;
+        x->grid[cls] = dc->sm_count * batch_ctas(dc, cls + 1, x->variant[cls]);
+    }
+    bool ok = true;
+    for (int b = 0; b < 2 && ok; ++b) {
+        ok = ok && cudaStreamCreateWithFlags(&x->streams[b], cudaStreamNonBlocking) == cudaSuccess;
+        ok = ok && cudaEventCreateWithFlags(&x->kdone[b], cudaEventDisableTiming) == cudaSuccess;
+    }
+    ok = ok && cudaMalloc(&x->d_mats, (size_t)cfg.max_jobs * kSlotBytes) == cudaSuccess;
+    ok = ok && cudaMalloc(&x->d_acc, (size_t)cfg.max_jobs * 2 * sizeof(unsigned long long)) == cudaSuccess;
+    ok = ok && cudaMalloc(&x->d_left, (size_t)cfg.max_jobs * sizeof(unsigned)) == cudaSuccess;
+    ok = ok && cudaMalloc(&x->d_results, (size_t)cfg.max_jobs) == cudaSuccess;
+    ok = ok && cudaMalloc(&x->d_cursor, 4 * sizeof(unsigned)) == cudaSuccess;
+    for (int b = 0; b < 2 && ok; ++b) {
+        ok = ok && cudaMalloc(&x->d_stage[b], (size_t)cfg.max_admit * kSlotBytes) == cudaSuccess;
+        ok = ok && cudaMalloc(&x->d_table[b], table_bytes(cfg)) == cudaSuccess;
+        ok = ok && cudaMallocHost(&x->h_stage[b], (size_t)cfg.max_admit * kSlotBytes) == cudaSuccess;
+        ok = ok && cudaMallocHost(&x->h_table[b], table_bytes(cfg)) == cudaSuccess;
+        ok = ok && cudaMallocHost(&x->h_results[b], (size_t)cfg.max_jobs) == cudaSuccess;
+        ok = ok && cudaEventCreateWithFlags(&x->ev[b], cudaEventDisableTiming) == cudaSuccess;
+    }
+    ok = ok && cudaMemset(x->d_results, kPending, (size_t)cfg.max_jobs) == cudaSuccess;
+    ok = ok && cudaDeviceSynchronize() == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        pf3_destroy(x);
+        return PF3_ENOMEM;
+    }
+    x->free_slots.reserve(cfg.max_jobs);
+    for (int sl = cfg.max_jobs - 1; sl >= 0; --sl) x->free_slots.push_back(sl);
+    x->th = std::thread(scheduler, x);
+    *out = x;
+    return PF3_OK;
+}
+
+void pf3_destroy(pf3_ctx* x)
+{
+    if (!x) return;
+    if (x->th.joinable()) {
+        {
+            std::lock_guard<std::mutex> g(x->mu);
+            x->stop = true;
+            // requests not yet admitted are cancelled; admitted ones finish
+            for (int64_t tk : x->pending) {
+                x->jobs[tk].state = kFailed;
+                x->jobs[tk].error = PF3_ECANCELED;
+            }
+            x->pending.clear();
+            x->cv_work.notify_all();
+            x->cv_done.notify_all();
+        }
+        x->th.join();
+    }
+    for (int b = 0; b < 2; ++b)
+        if (x->streams[b]) cudaStreamSynchronize(x->streams[b]);
+    cudaFree(x->d_mats);
+    cudaFree(x->d_acc);
+    cudaFree(x->d_left);
+    cudaFree(x->d_results);
+    cudaFree(x->d_cursor);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(x->d_stage[b]);
+        cudaFree(x->d_table[b]);
+        cudaFreeHost(x->h_stage[b]);
+        cudaFreeHost(x->h_table[b]);
+        cudaFreeHost(x->h_results[b]);
+        if (x->ev[b]) cudaEventDestroy(x->ev[b]);
+    }
+    for (int b = 0; b < 2; ++b) {
+        if (x->kdone[b]) cudaEventDestroy(x->kdone[b]);
+        if (x->streams[b]) cudaStreamDestroy(x->streams[b]);
+    }
+    delete x;
+}
+
+int pf3_cancel_queued(pf3_ctx* x)
+{
+    if (!x) return PF3_EINVAL;
+    std::lock_guard<std::mutex> g(x->mu);
+    int cnt = 0;
+    for (int64_t tk : x->pending) {
+        x->jobs[tk].state = kFailed;
+        x->jobs[tk].error = PF3_ECANCELED;
+        x->jobs[tk].t_done = now_ns();
+        ++cnt;
+    }
+    x->pending.clear();
+    x->cv_done.notify_all();
+    return cnt;
+}
+
+int64_t perm_f3_submit(pf3_ctx* x, const uint8_t* A, int n)
+{
+    if (!x || n < 0 || n > PF3_MAX_N || (n > 0 && !A)) return PF3_EINVAL;
+    for (int k = 0; k < n * n; ++k)
+        if (A[k] > 2) return PF3_EDOMAIN;
+    std::lock_guard<std::mutex> g(x->mu);
+    if (x->stop) return PF3_ECANCELED;
+    if (x->fatal) return x->fatal;
+    if ((int64_t)x->pending.size() >= x->cfg.queue_depth) return PF3_EBUSY;
+    const int64_t tk = (int64_t)x->jobs.size();
+    x->jobs.emplace_back();
+    Job& j = x->jobs.back();
+    j.n = n;
+    j.t_submit = now_ns();
+    if (n == 0) {
+        j.state = kDone;
+        j.result = 1;
+        j.t_done = j.t_submit;
+        ++x->done;
+        x->cv_done.notify_all();
+        return tk;
+    }
+    j.A.assign(A, A + (size_t)n * n);
+    x->pending.push_back(tk);
+    x->cv_work.notify_one();
+    return tk;
+}
+
+int perm_f3_poll(pf3_ctx* x, int64_t ticket, uint8_t* result)
+{
+    if (!x) return PF3_EINVAL;
+    std::lock_guard<std::mutex> g(x->mu);
+    if (ticket < 0 || ticket >= (int64_t)x->jobs.size()) return PF3_EINVAL;
+    const Job& j = x->jobs[ticket];
+    if (j.state == kDone) {
+        if (result) *result = (uint8_t)j.result;
+        return PF3_OK;
+    }
+    if (j.state == kFailed) return j.error;
+    return PF3_PENDING;
+}
+
+int perm_f3_wait(pf3_ctx* x, int64_t ticket, uint8_t* result, int64_t timeout_us)
+{
+    if (!x) return PF3_EINVAL;
+    std::unique_lock<std::mutex> lk(x->mu);
+    if (ticket < 0 || ticket >= (int64_t)x->jobs.size()) return PF3_EINVAL;
+    auto ready = [&] { return x->jobs[ticket].state >= kDone; };
+    if (timeout_us < 0) {
+        x->cv_done.wait(lk, ready);
+    } else if (!x->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready)) {
+        return PF3_ETIMEDOUT;
+    }
+    const Job& j = x->jobs[ticket];
+    if (j.state == kFailed) return j.error;
+    if (result) *result = (uint8_t)j.result;
+    return PF3_OK;
+}
+
+int pf3_job_times(pf3_ctx* x, int64_t ticket, uint64_t* submit_ns, uint64_t* done_ns)
+{
+    if (!x) return PF3_EINVAL;
+    std::lock_guard<std::mutex> g(x->mu);
+    if (ticket < 0 || ticket >= (int64_t)x->jobs.size()) return PF3_EINVAL;
+    const Job& j = x->jobs[ticket];
+    if (submit_ns) *submit_ns = j.t_submit;
+    if (done_ns) *done_ns = j.t_done;
+    return j.state >= kDone ? PF3_OK : PF3_PENDING;
+}
+
+int pf3_serve_stats(pf3_ctx* x, uint64_t* launches, uint64_t* items, uint64_t* jobs_done)
+{
+    if (!x) return PF3_EINVAL;
+    std::lock_guard<std::mutex> g(x->mu);
+    if (launches) *launches = x->launches;
+    if (items) *items = x->items;
+    if (jobs_done) *jobs_done = x->done;
+    return PF3_OK;
+}
+
+uint64_t pf3_now_ns(void) { return now_ns(); }
+
+}  // extern "C"
