@@ -9,7 +9,12 @@ through the host-pointer C entry point perm_f3 (input copied in, result
 copied out, every call).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--no-batch] [--no-cpu-baseline]
+                  [--no-batch] [--no-cpu-baseline] [--no-serve] [--serve-jobs J] [--long]
+
+Secondary measurements go under "extra": the batched Monte Carlo workload
+(200,000 seeded 24 x 24 matrices in one call, against the same matrices one
+launch each), the serving mix (Poisson arrivals, n in 12..40, against FIFO one
+matrix per launch) and, with --long, the seeded 48 x 48 matrix.
 
 With N > 1 (torchrun, one rank per GPU) every rank walks its 1/N share of each
 matrix's Gray range (Sec. 3.1's block split) and the two 64-bit counts are
@@ -43,6 +48,44 @@ def i_alg(W: int, G: int = G_LOG2) -> float:
     2^G indices, one full row step on the base (3 LOP3 per word), 2^G - 1
     probes on the low mag word (2 LOP3 each) and 2^G zero tests (one compare)."""
     return (3 * W + 2 * ((1 << G) - 1) + (1 << G)) / (1 << G)
+
+
+KERNEL_FILES = {"single": ("pf3_device.cuh", "pf3_internal.h", "pf3_single.cu"),
+                "batch": ("pf3_device.cuh", "pf3_internal.h", "pf3_batch.h", "pf3_batch.cu")}
+
+
+def kernel_source_hash(kind: str = "single") -> str:
+    """Hash of the sources a kernel is compiled from: ties a committed ncu
+    summary to the kernel it measured."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2407_20205_gb300", "csrc")
+    for name in KERNEL_FILES[kind]:
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(summary="walk_single_n36.md"):
+    """DRAM bytes per launch from the committed ncu summary of the walk kernel,
+    or None when the kernel sources changed since that capture."""
+    path = os.path.join(ROOT, "profiles", summary)
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        line = line.strip().lstrip("-* ")
+        if ":" in line and line.startswith(("source_hash", "dram_bytes_per_launch")):
+            k, v = line.split(":", 1)
+            vals[k.strip(" `")] = v.strip(" `")
+    if vals.get("source_hash") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 def dist_env():
@@ -277,7 +320,7 @@ def run_ours(args):
         lanes = float(os.environ.get("PF3_ALU_LANES", "64"))
         peak = n_sm * sm_max * 1e6 * lanes / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-                "traffic": None,
+                "traffic": profiled_traffic(),
                 "note": f"ops = {i_alg(2)} ALU instructions per subset (W=2 grouped walk); peak = {n_sm} SMs x "
                         f"{sm_max:.0f} MHz x {lanes:.0f} lanes/clk/SM (LOP3/ISETP issue), of measured clock"}
         # e2e through the host-pointer C entry point (copies in and out each call)
@@ -297,6 +340,13 @@ def run_ours(args):
         extra = {}
         if not args.no_batch and world == 1:
             extra["batch_n24"] = bench_batch(pf3, torch, dev, stream)
+            extra["batch_n24"]["one_matrix_per_launch"] = bench_single_launches(pf3, torch, dev, stream)
+        if not args.no_serve and world == 1:
+            from paper_2407_20205_gb300 import serve
+            out, _, _ = serve.run(jobs=args.serve_jobs, nmin=12, nmax=40, rho=0.7, capacity=value)
+            extra["serve"] = out
+        if args.long and world == 1:
+            extra["long_n48"] = bench_long(pf3)
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             cpu = cpu_sample(mats[36])
@@ -346,6 +396,38 @@ def bench_batch(pf3, torch, dev, stream, count=200000):
             "alu_frac": sub_s * i_alg(1) / peak_ops}
 
 
+def bench_single_launches(pf3, torch, dev, stream, count=2000):
+    """The plain form for comparison: the same n = 24 matrices, one launch each."""
+    from paper_2407_20205_gb300 import inputs
+    A = inputs.uniform_matrices(inputs.SEED_BATCH24, 24, count)
+    dA = torch.from_numpy(A).to(dev)
+    out = torch.zeros((count, 3), dtype=torch.int64, device=dev)
+    last = (1 << 24) - 1
+    with torch.cuda.stream(stream):
+        for k in range(8):
+            pf3.perm_f3_range_counts_async(dA[k], 24, 0, last, out[k], stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(count):
+            pf3.perm_f3_range_counts_async(dA[k], 24, 0, last, out[k], stream)
+        e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1)
+    return {"matrices": count, "ms": ms, "perms_per_s": count / (ms * 1e-3),
+            "subsets_per_s": count * (1 << 24) / (ms * 1e-3)}
+
+
+def bench_long(pf3):
+    """48 x 48 seeded uniform matrix, all 2^48 Gray indices in bounded launches."""
+    from paper_2407_20205_gb300 import inputs
+    A = inputs.uniform_matrix(inputs.SEED_N48, 48)
+    t0 = time.perf_counter()
+    r = pf3.longrun(A, chunk_log2=44)
+    dt = time.perf_counter() - t0
+    return {"n": 48, "seconds": dt, "subsets_per_s": (1 << 48) / dt, "perm": r.get("perm"),
+            "plus": r["plus"], "minus": r["minus"], "launches": 1 << 4}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -354,6 +436,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-jobs", type=int, default=600)
+    ap.add_argument("--long", action="store_true", help="also walk the seeded 48x48 matrix (about a minute)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -112,9 +112,10 @@ int perm_f3_range_counts_noalloc(const uint8_t* dA, int n, uint64_t first, uint6
  * checkpoint_path (temporary file + rename; NULL = no checkpoint).  If the
  * file already holds a checkpoint of the same matrix, the walk resumes from
  * it; one of another matrix is refused (PF3_EINVAL).  Stops between launches
- * when max_seconds (> 0) of wall time have passed (PF3_ETIMEDOUT) or when
- * pf3_longrun_cancel(1) was called (PF3_ECANCELED); the counts so far are
- * returned and saved either way.  *finished = 1 once the whole range is done;
+ * when max_seconds (> 0) of wall time have passed (PF3_ETIMEDOUT; checked
+ * after each launch, so every call makes at least one launch of progress) or
+ * when pf3_longrun_cancel(1) was called (PF3_ECANCELED; checked before each
+ * launch); the counts so far are returned and saved either way.  *finished = 1 once the whole range is done;
  * *next_index is the first index not yet walked (0 when finished). */
 int pf3_longrun(const uint8_t* A, int n, int chunk_log2, const char* checkpoint_path, double max_seconds,
                 uint64_t* plus, uint64_t* minus, uint64_t* next_index, int* finished);

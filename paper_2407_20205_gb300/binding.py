@@ -324,7 +324,7 @@ class ServeContext:
         return int(a.value), int(b.value)
 
     def cancel_queued(self) -> int:
-        return _check(_lib_cancel(self._h), "pf3_cancel_queued", "pf3_longrun", "pf3_longrun_cancel")
+        return _check(_lib_cancel(self._h), "pf3_cancel_queued")
 
     def stats(self) -> dict:
         a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()

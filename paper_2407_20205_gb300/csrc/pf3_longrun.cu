@@ -120,11 +120,6 @@ int pf3_longrun(const uint8_t* A, int n, int chunk_log2, const char* checkpoint_
             rc = PF3_ECANCELED;
             break;
         }
-        const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-        if (max_seconds > 0 && el >= max_seconds) {
-            rc = PF3_ETIMEDOUT;
-            break;
-        }
         const uint64_t first = ck.cursor;
         const uint64_t stop = (last - first <= step_m1) ? last : first + step_m1;
         if ((rc = enqueue_range(c, c->d_A, n, first, stop, c->d_out, c->stream))) break;
@@ -139,6 +134,9 @@ int pf3_longrun(const uint8_t* A, int n, int chunk_log2, const char* checkpoint_
             rc = PF3_EINVAL;
             break;
         }
+        // the wall-clock limit is checked after each launch: every call makes progress
+        const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (!ck.done && max_seconds > 0 && el >= max_seconds) rc = PF3_ETIMEDOUT;
     }
     *plus = ck.plus;
     *minus = ck.minus;
