@@ -109,14 +109,6 @@ def matrices():
     return {n: inputs.uniform_matrix(seeds[n], n) for n in SIZES}
 
 
-def rank_range(n, rank, world):
-    total = 1 << n
-    q, r = divmod(total, world)
-    a = rank * q + min(rank, r)
-    ln = q + (1 if rank < r else 0)
-    return a, a + ln - 1
-
-
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -248,7 +240,8 @@ def run_ours(args):
     out = {n: torch.zeros(3, dtype=torch.int64, device=dev) for n in SIZES}
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
-    ranges = {n: rank_range(n, rank, world) for n in SIZES}
+    from paper_2407_20205_gb300 import multirank
+    ranges = {n: multirank.rank_range(n, rank, world) for n in SIZES}
 
     def step():
         for n in SIZES:
