@@ -136,9 +136,19 @@ int perm_f3_batch(const uint8_t* As, const int32_t* ns, int64_t count, uint8_t* 
 /* Device-pointer batch: dAs, d_results (count bytes) and d_hist (3 x uint64,
  * overwritten) on the device; ns and the matrix offsets are read from the HOST
  * array ns (the library builds its work plan from them).  Stream-ordered on
- * `stream`; an entry outside {0,1,2} gives result 255 for that matrix. */
+ * `stream`; an entry outside {0,1,2} gives result 255 for that matrix.  The
+ * launch sequence (item-table upload, counter resets, one persistent kernel
+ * per plane width) is captured as a CUDA graph; a later call with the same ns,
+ * pointers and tuning replays the graph without re-planning, reading the
+ * current contents of dAs. */
 int perm_f3_batch_async(const uint8_t* dAs, const int32_t* ns, int64_t count, uint8_t* d_results,
                         uint64_t* d_hist, void* stream);
+
+/* Table 2 (Sec. 4): perm mod 3 of every one of the 3^(n^2) matrices in
+ * F3^{n x n}, n in 1..5, counted by value: counts[v] = #{A : perm(A) = v}
+ * (counts[0] = z(n)).  Matrices are generated on the device from their
+ * index; runs in bounded launches (n = 5: 8.47e11 matrices). */
+int pf3_count_exhaustive(int n, uint64_t* counts);
 
 /* ------------------------------------------------------------ serving */
 

@@ -206,6 +206,18 @@ def perm_f3_batch_async(dAs, ns, d_results, d_hist, stream=None) -> None:
            "perm_f3_batch_async")
 
 
+# ------------------------------------------------------------ Table 2
+
+_lib_zcount = _sig("pf3_count_exhaustive", ctypes.c_int, [ctypes.c_int, _u64p])
+
+
+def count_exhaustive(n: int) -> tuple[int, int, int]:
+    """(#perm=0, #perm=1, #perm=2) over all 3^(n^2) matrices, n <= 5."""
+    c = (ctypes.c_uint64 * 3)()
+    _check(_lib_zcount(n, c), "pf3_count_exhaustive")
+    return int(c[0]), int(c[1]), int(c[2])
+
+
 # ------------------------------------------------------------ long runs
 
 _lib_longrun = _sig("pf3_longrun", ctypes.c_int,
@@ -406,5 +418,6 @@ def exported_symbols() -> list[str]:
                         "pf3_set_batch_split", "pf3_autotune", "perm_f3_range_counts_noalloc",
                         "pf3_config_default", "pf3_create", "pf3_destroy", "perm_f3_submit", "perm_f3_poll",
                         "perm_f3_wait", "pf3_job_times", "pf3_serve_stats", "pf3_now_ns",
-                        "pf3_cancel_queued", "pf3_longrun", "pf3_longrun_cancel")
+                        "pf3_cancel_queued", "pf3_longrun", "pf3_longrun_cancel",
+                        "pf3_count_exhaustive")
             if hasattr(_lib, n)]

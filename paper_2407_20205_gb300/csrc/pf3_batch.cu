@@ -30,12 +30,55 @@ namespace {
 
 constexpr unsigned kBadBit = 0x80000000u;
 
+// Per-lane row masks of one tiny matrix: [row][component][lane], component
+// 0 = K1, 1 = K2 (add), 2 = K2 (subtract).
+struct TinyTable {
+    uint32_t k[kTinyN][3][32];
+};
+
+// One lane: pack its n x n matrix (n <= kTinyN) and walk all 2^n Gray
+// indices with the row step of Sec. 2 (Theorem 2.1 semantics), full zero test
+// and popcount sign at every index.  Returns perm mod 3, or 255 on a bad entry.
+__device__ __forceinline__ int tiny_perm(TinyTable& T, const uint8_t* A, int n, int lane)
+{
+    bool bad = false;
+    for (int r = 0; r < n; ++r) {
+        uint32_t mag = 0, sgn = 0;
+        for (int c = 0; c < n; ++c) {
+            const uint32_t v = A[r * n + c];
+            bad |= v > 2u;
+            mag |= (uint32_t)(v == 1u || v == 2u) << c;
+            sgn |= (uint32_t)(v == 2u) << c;
+        }
+        uint32_t k1, k2p, k2m;
+        row_masks(mag, sgn, k1, k2p, k2m);
+        T.k[r][0][lane] = k1;
+        T.k[r][1][lane] = k2p;
+        T.k[r][2][lane] = k2m;
+    }
+    if (bad) return 255;
+    uint32_t m = ~((1u << n) - 1u), s = 0u;  // zero vector, padding columns = 1
+    unsigned long long p = 0, q = 0;
+    const uint32_t last = (1u << n) - 1u;
+    for (uint32_t i = 1; i <= last; ++i) {
+        const int t = __ffs((int)i) - 1;
+        const int dir = (int)((i >> (t + 1)) & 1u);
+        add_word(m, s, T.k[t][0][lane], T.k[t][1 + dir][lane]);
+        if (m == 0xFFFFFFFFu) {
+            if ((__popc(s) + i) & 1u) ++q;
+            else ++p;
+        }
+    }
+    return (int)perm_from_counts(n, p, q);
+}
+
 template <int W, int U, int MINB>
 __global__ void __launch_bounds__(kBatchThreads, MINB) batch_kernel(BatchArgs a)
 {
     constexpr int G = kGroupLog2;
     __shared__ RowTable<W> tabs[kBatchThreads / 32];
     __shared__ WarpQueue<W> queues[kBatchThreads / 32];
+    __shared__ TinyTable tiny[W == 1 ? kBatchThreads / 32 : 1];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     RowTable<W>& tab = tabs[warp];
@@ -51,6 +94,23 @@ __global__ void __launch_bounds__(kBatchThreads, MINB) batch_kernel(BatchArgs a)
         const WorkItem it = a.items[item];
         const int n = it.n;
         const uint8_t* A = a.As + it.offset;
+
+        if (W == 1 && it.split == kTinyItem) {
+            // a group of up to 32 small matrices: one per lane
+            int r = -1;
+            if ((unsigned long long)lane < it.NB) {
+                r = (n == 0) ? 1 : tiny_perm(tiny[warp], A + (size_t)lane * n * n, n, lane);
+                a.results[it.mat + lane] = (uint8_t)r;
+            }
+            if (a.hist) {
+                for (int v = 0; v < 3; ++v) {
+                    const unsigned cnt = __popc(__ballot_sync(0xFFFFFFFFu, r == v));
+                    if (lane == 0 && cnt) atomicAdd(a.hist + v, (unsigned long long)cnt);
+                }
+            }
+            __syncwarp();
+            continue;
+        }
 
         bool bad = false;
         const int rows = n > U ? n : U;
@@ -179,6 +239,23 @@ void plan_batch(const int32_t* ns, int64_t count, const BatchTuning& tune, Batch
     long long off = 0;
     for (int64_t k = 0; k < count; ++k) {
         const int n = ns[k];
+        if (n <= kTinyN) {
+            // a run of up to 32 consecutive matrices with this same small n
+            int64_t e = k + 1;
+            while (e < count && e - k < 32 && ns[e] == n) ++e;
+            WorkItem it;
+            std::memset(&it, 0, sizeof(it));
+            it.offset = off;
+            it.mat = (int)k;
+            it.n = n;
+            it.split = kTinyItem;
+            it.B0 = 0;
+            it.NB = (unsigned long long)(e - k);
+            plan.items[0].push_back(it);
+            off += (long long)n * n * (e - k);
+            k = e - 1;
+            continue;
+        }
         WorkItem it;
         std::memset(&it, 0, sizeof(it));
         it.offset = off;
@@ -214,10 +291,16 @@ void plan_batch(const int32_t* ns, int64_t count, const BatchTuning& tune, Batch
         }
     }
     plan.total_bytes = off;
-    // largest first (longest-processing-time order); ties keep matrix order
+    // largest first (longest-processing-time order); ties keep matrix order.
+    // Cost = Gray indices one warp walks (a tiny item's lanes run in parallel).
     for (int cls = 0; cls < 2; ++cls) {
+        const int U = Ucls[cls];
+        auto cost = [U](const WorkItem& x) -> unsigned long long {
+            if (x.split == kTinyItem || x.NB == 0) return 1ull << x.n;
+            return (unsigned long long)x.NB << U;
+        };
         std::stable_sort(plan.items[cls].begin(), plan.items[cls].end(),
-                         [](const WorkItem& x, const WorkItem& y) { return x.NB > y.NB; });
+                         [&](const WorkItem& x, const WorkItem& y) { return cost(x) > cost(y); });
     }
 }
 
@@ -263,8 +346,58 @@ static int ensure_batch_scratch(DeviceCtx* c, size_t items, size_t splits, size_
     return PF3_OK;
 }
 
-// enqueue a planned batch on `stream`: upload the item table and split
-// counters, reset cursors and histogram, launch one persistent grid per class
+// device buffers one batch launch sequence works on
+struct BatchBufs {
+    const WorkItem* d_items;       // class W = 2 items first, then W = 1
+    unsigned long long* d_acc;
+    unsigned* d_left;
+    unsigned* d_cursor;
+    const void* h_items;           // pinned source of the item table
+    const unsigned* h_left;        // source of the split item counts
+};
+
+// the launch sequence itself: upload the item table and split counters, reset
+// cursors and histogram, one persistent grid per plane width (W = 2 first)
+static int enqueue_batch_core(DeviceCtx* c, const BatchPlan& plan, const BatchBufs& bb, const uint8_t* dAs,
+                              uint8_t* d_results, unsigned long long* d_hist, cudaStream_t stream)
+{
+    const size_t n0 = plan.items[0].size(), n1 = plan.items[1].size();
+    cudaError_t e = cudaSuccess;
+    if (n0 + n1)
+        e = cudaMemcpyAsync((void*)bb.d_items, bb.h_items, (n0 + n1) * sizeof(WorkItem), cudaMemcpyHostToDevice,
+                            stream);
+    if (e == cudaSuccess && plan.num_split) {
+        e = cudaMemsetAsync(bb.d_acc, 0, (size_t)plan.num_split * 2 * sizeof(unsigned long long), stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(bb.d_left, bb.h_left, (size_t)plan.num_split * sizeof(unsigned int),
+                                cudaMemcpyHostToDevice, stream);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(bb.d_cursor, 0, 4 * sizeof(unsigned int), stream);
+    if (e == cudaSuccess && d_hist) e = cudaMemsetAsync(d_hist, 0, 3 * sizeof(unsigned long long), stream);
+    if (e != cudaSuccess) return cuda_rc(e);
+    BatchArgs a;
+    a.As = dAs;
+    a.results = d_results;
+    a.hist = d_hist;
+    a.acc = bb.d_acc;
+    a.left = bb.d_left;
+    for (int cls = 1; cls >= 0; --cls) {
+        const size_t cnt = plan.items[cls].size();
+        if (!cnt) continue;
+        a.items = bb.d_items + (cls == 1 ? 0 : n1);
+        a.num_items = (unsigned)cnt;
+        a.cursor = bb.d_cursor + cls;
+        const int v = c->tune.variant[cls];
+        const int per_sm = batch_ctas(c, cls + 1, v);
+        int grid = c->sm_count * per_sm;
+        const size_t ctas_needed = (cnt + kBatchThreads / 32 - 1) / (kBatchThreads / 32);
+        if ((size_t)grid > ctas_needed) grid = (int)ctas_needed;
+        if ((e = launch_batch(cls == 0 ? 1 : 2, v, a, grid, stream)) != cudaSuccess) return cuda_rc(e);
+    }
+    return PF3_OK;
+}
+
+// enqueue a planned batch on `stream` using the context's batch scratch
 int enqueue_batch(DeviceCtx* c, const BatchPlan& plan, const uint8_t* dAs, uint8_t* d_results,
                   unsigned long long* d_hist, cudaStream_t stream)
 {
@@ -278,38 +411,91 @@ int enqueue_batch(DeviceCtx* c, const BatchPlan& plan, const uint8_t* dAs, uint8
     if (e != cudaSuccess) return cuda_rc(e);
     if (n1) std::memcpy(h, plan.items[1].data(), n1 * sizeof(WorkItem));
     if (n0) std::memcpy(h + n1, plan.items[0].data(), n0 * sizeof(WorkItem));
-    if (n0 + n1)
-        e = cudaMemcpyAsync(b.d_items, h, (n0 + n1) * sizeof(WorkItem), cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess && plan.num_split) {
-        e = cudaMemsetAsync(b.d_acc, 0, (size_t)plan.num_split * 2 * sizeof(unsigned long long), stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(b.d_left, plan.split_items.data(), (size_t)plan.num_split * sizeof(unsigned int),
-                                cudaMemcpyHostToDevice, stream);
-    }
-    if (e == cudaSuccess) e = cudaMemsetAsync(b.d_cursor, 0, 4 * sizeof(unsigned int), stream);
-    if (e == cudaSuccess && d_hist) e = cudaMemsetAsync(d_hist, 0, 3 * sizeof(unsigned long long), stream);
+    BatchBufs bb{(const WorkItem*)b.d_items, b.d_acc, b.d_left, b.d_cursor, h, plan.split_items.data()};
+    return enqueue_batch_core(c, plan, bb, dAs, d_results, d_hist, stream);
+}
+
+static void free_graph(BatchGraphCache& g)
+{
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+    cudaFreeHost(g.h_items);
+    cudaFreeHost(g.h_left);
+    cudaFree(g.d_items);
+    cudaFree(g.d_acc);
+    cudaFree(g.d_left);
+    cudaFree(g.d_cursor);
+    g = BatchGraphCache();
+}
+
+static bool same_tuning(const BatchTuning& a, const BatchTuning& b)
+{
+    return a.cutoff == b.cutoff && a.chunk_log2 == b.chunk_log2 && a.variant[0] == b.variant[0] &&
+           a.variant[1] == b.variant[1];
+}
+
+// Replay the captured launch sequence when nothing changed, else plan,
+// capture on a private stream, instantiate and launch.
+int enqueue_batch_graph(DeviceCtx* c, const int32_t* ns, int64_t count, const uint8_t* dAs, uint8_t* d_results,
+                        unsigned long long* d_hist, cudaStream_t stream)
+{
+    BatchGraphCache& g = c->bgraph;
+    if (g.valid && (int64_t)g.ns.size() == count && g.dAs == dAs && g.d_results == d_results && g.d_hist == d_hist &&
+        same_tuning(g.tune, c->tune) && std::memcmp(g.ns.data(), ns, (size_t)count * sizeof(int32_t)) == 0)
+        return cuda_rc(cudaGraphLaunch(g.exec, stream));
+    // a previous replay may still read the buffers about to be freed
+    cudaError_t e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return cuda_rc(e);
-    BatchArgs a;
-    a.As = dAs;
-    a.results = d_results;
-    a.hist = d_hist;
-    a.acc = b.d_acc;
-    a.left = b.d_left;
-    for (int cls = 1; cls >= 0; --cls) {
-        const size_t cnt = plan.items[cls].size();
-        if (!cnt) continue;
-        a.items = (const WorkItem*)b.d_items + (cls == 1 ? 0 : n1);
-        a.num_items = (unsigned)cnt;
-        a.cursor = b.d_cursor + cls;
-        const int v = c->tune.variant[cls];
-        const int per_sm = batch_ctas(c, cls + 1, v);
-        int grid = c->sm_count * per_sm;
-        const size_t warps_needed = cnt;
-        const size_t ctas_needed = (warps_needed + kBatchThreads / 32 - 1) / (kBatchThreads / 32);
-        if ((size_t)grid > ctas_needed) grid = (int)ctas_needed;
-        if ((e = launch_batch(cls == 0 ? 1 : 2, v, a, grid, stream)) != cudaSuccess) return cuda_rc(e);
+    if (g.valid || g.exec) free_graph(g);
+    BatchPlan plan;
+    plan_batch(ns, count, c->tune, plan);
+    const size_t n0 = plan.items[0].size(), n1 = plan.items[1].size();
+    const size_t ns_split = (size_t)plan.num_split + 1;
+    bool ok = cudaMallocHost(&g.h_items, std::max<size_t>(1, n0 + n1) * sizeof(WorkItem)) == cudaSuccess;
+    ok = ok && cudaMallocHost(&g.h_left, ns_split * sizeof(unsigned)) == cudaSuccess;
+    ok = ok && cudaMalloc(&g.d_items, std::max<size_t>(1, n0 + n1) * sizeof(WorkItem)) == cudaSuccess;
+    ok = ok && cudaMalloc(&g.d_acc, ns_split * 2 * sizeof(unsigned long long)) == cudaSuccess;
+    ok = ok && cudaMalloc(&g.d_left, ns_split * sizeof(unsigned)) == cudaSuccess;
+    ok = ok && cudaMalloc(&g.d_cursor, 4 * sizeof(unsigned)) == cudaSuccess;
+    if (ok && !c->capture_stream)
+        ok = cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_graph(g);
+        return PF3_ENOMEM;
     }
-    return PF3_OK;
+    WorkItem* h = (WorkItem*)g.h_items;
+    if (n1) std::memcpy(h, plan.items[1].data(), n1 * sizeof(WorkItem));
+    if (n0) std::memcpy(h + n1, plan.items[0].data(), n0 * sizeof(WorkItem));
+    if (plan.num_split) std::memcpy(g.h_left, plan.split_items.data(), (size_t)plan.num_split * sizeof(unsigned));
+    BatchBufs bb{(const WorkItem*)g.d_items, g.d_acc, g.d_left, g.d_cursor, g.h_items, g.h_left};
+    e = cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        free_graph(g);
+        return cuda_rc(e);
+    }
+    int rc = enqueue_batch_core(c, plan, bb, dAs, d_results, d_hist, c->capture_stream);
+    e = cudaStreamEndCapture(c->capture_stream, &g.graph);
+    if (rc || e != cudaSuccess) {
+        cudaGetLastError();
+        free_graph(g);
+        return rc ? rc : cuda_rc(e);
+    }
+    e = cudaGraphInstantiate(&g.exec, g.graph, 0);
+    if (e != cudaSuccess) {
+        free_graph(g);
+        return cuda_rc(e);
+    }
+    g.ns.assign(ns, ns + count);
+    g.dAs = dAs;
+    g.d_results = d_results;
+    g.d_hist = d_hist;
+    g.tune = c->tune;
+    g.n_items[0] = (int)n0;
+    g.n_items[1] = (int)n1;
+    g.num_split = plan.num_split;
+    g.valid = true;
+    return cuda_rc(cudaGraphLaunch(g.exec, stream));
 }
 
 }  // namespace pf3
@@ -379,9 +565,7 @@ int perm_f3_batch_async(const uint8_t* dAs, const int32_t* ns, int64_t count, ui
             return cuda_rc(cudaMemsetAsync(d_hist, 0, 3 * sizeof(unsigned long long), (cudaStream_t)stream));
         return PF3_OK;
     }
-    BatchPlan& plan = c->last_plan;
-    plan_batch(ns, count, c->tune, plan);
-    return enqueue_batch(c, plan, dAs, d_results, (unsigned long long*)d_hist, (cudaStream_t)stream);
+    return enqueue_batch_graph(c, ns, count, dAs, d_results, (unsigned long long*)d_hist, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -9,9 +9,13 @@
 namespace pf3 {
 
 constexpr int kBatchThreads = 128;  // 4 warps, one instance per warp
+constexpr int kTinyN = 10;          // n <= kTinyN: one matrix per lane (32 per item)
+constexpr int kTinyItem = -2;       // WorkItem.split of a group of tiny matrices
 
 // One unit of batch work: Gray blocks [B0, B0 + NB) of matrix `mat` (block =
 // 2^U indices); NB == 0 means "all 2^n indices, walked by one lane" (n <= U).
+// A tiny item (split == kTinyItem) is NB <= 32 consecutive matrices of the
+// same n <= kTinyN starting at `mat` / `offset`: lane k walks matrix mat + k.
 struct WorkItem {
     long long offset;         // byte offset of the matrix in the batch buffer
     unsigned long long B0;

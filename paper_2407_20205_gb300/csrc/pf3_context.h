@@ -4,6 +4,7 @@
 
 #include <cstdint>
 #include <mutex>
+#include <vector>
 
 #include "pf3_batch.h"
 
@@ -27,6 +28,27 @@ struct BatchScratch {
     size_t h_items_cap = 0;
 };
 
+// The launch sequence of the last device-pointer batch, captured as a CUDA
+// graph and replayed while the plan (sizes, pointers, tuning) is unchanged.
+struct BatchGraphCache {
+    bool valid = false;
+    std::vector<int32_t> ns;
+    const uint8_t* dAs = nullptr;
+    uint8_t* d_results = nullptr;
+    unsigned long long* d_hist = nullptr;
+    BatchTuning tune;
+    int n_items[2] = {0, 0};
+    int num_split = 0;
+    void* h_items = nullptr;               // pinned, owned by the graph
+    unsigned* h_left = nullptr;            // pinned, owned by the graph
+    void* d_items = nullptr;
+    unsigned long long* d_acc = nullptr;
+    unsigned* d_left = nullptr;
+    unsigned* d_cursor = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
 struct DeviceCtx {
     int device = 0;
     int sm_count = 0;
@@ -43,8 +65,9 @@ struct DeviceCtx {
     uint8_t* h_A = nullptr;                   // pinned
     unsigned long long* h_out = nullptr;      // pinned
     BatchScratch batch;
+    BatchGraphCache bgraph;
+    cudaStream_t capture_stream = nullptr;
     BatchTuning tune;
-    BatchPlan last_plan;
     std::mutex mu;
 };
 

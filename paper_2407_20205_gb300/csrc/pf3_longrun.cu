@@ -7,7 +7,7 @@
 // 2^chunk_log2 indices; after each launch the exact 64-bit counts and the
 // next index are written to a checkpoint file (written to a temporary name,
 // then renamed), so an interrupted run resumes where it stopped and produces
-// the same counts as an uninterrupted one.  Between launches the driver
+// the same counts as an uninterrupted one.  Between launches the loop
 // honours a wall-clock limit and a cancellation flag; no launch waits on the
 // host.
 #include <cuda_runtime.h>

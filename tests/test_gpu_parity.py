@@ -327,3 +327,32 @@ def test_autotune_keeps_results(pf3, oracle):
     assert all(t > 0 for t in rep["single_ms"][1] + rep["single_ms"][2])
     A = inputs.uniform_matrix(8300, 21)
     assert pf3.perm_f3_counts(A) == oracle.counts(T(A))
+
+
+def test_batch_async_graph_replay(pf3, oracle):
+    """Second identical call replays the captured graph and sees new matrix
+    contents; a different size list re-plans."""
+    import torch
+    n, count = 14, 64
+    A = inputs.uniform_matrices(9100, n, count)
+    B = inputs.uniform_matrices(9101, n, count)
+    ns = np.full(count, n, np.int32)
+    dAs = torch.from_numpy(A.reshape(-1).copy()).cuda()
+    res = torch.zeros(count, dtype=torch.uint8, device="cuda")
+    hist = torch.zeros(3, dtype=torch.int64, device="cuda")
+    s = torch.cuda.Stream()
+    want_a = oracle.perm_batch(list(A))
+    want_b = oracle.perm_batch(list(B))
+    for _ in range(2):
+        pf3.perm_f3_batch_async(dAs, ns, res, hist, s)
+        s.synchronize()
+        assert res.cpu().numpy().tolist() == want_a.tolist()
+    dAs.copy_(torch.from_numpy(B.reshape(-1).copy()).cuda())
+    pf3.perm_f3_batch_async(dAs, ns, res, hist, s)
+    s.synchronize()
+    assert res.cpu().numpy().tolist() == want_b.tolist()
+    assert hist.cpu().tolist() == [int((want_b == v).sum()) for v in range(3)]
+    ns2 = np.full(count // 2, n, np.int32)
+    pf3.perm_f3_batch_async(dAs, ns2, res, hist, s)
+    s.synchronize()
+    assert res[:count // 2].cpu().numpy().tolist() == want_b[:count // 2].tolist()

@@ -1,0 +1,50 @@
+"""The paper's Sec. 4 tables reproduced through the CUDA path: Table 2 exactly
+(every matrix for n <= 5), Table 3 statistically (seeded uniform samples)."""
+import math
+
+import pytest
+
+from conftest import read_golden
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pf3():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2407_20205_gb300 import binding
+    return binding
+
+
+def test_table2_small_exact(pf3, oracle):
+    z = {int(r[0]): int(r[1]) for r in read_golden("table2_zn.txt")}
+    for n in (1, 2, 3, 4):
+        c0, c1, c2 = pf3.count_exhaustive(n)
+        assert c0 == z[n]
+        assert c1 == c2                      # the row-negation bijection of Sec. 4
+        assert c0 + c1 + c2 == 3 ** (n * n)
+        if n <= 3:
+            assert (c0, c1, c2) == oracle.count_exhaustive(n)
+
+
+def test_table2_n5_exact(pf3):
+    """All 3^25 = 8.47e11 matrices of size 5: z(5) = 317,193,401,763."""
+    z = {int(r[0]): int(r[1]) for r in read_golden("table2_zn.txt")}
+    c0, c1, c2 = pf3.count_exhaustive(5)
+    assert c0 == z[5] == 317193401763
+    assert c1 == c2
+    assert c0 + c1 + c2 == 3 ** 25
+
+
+@pytest.mark.parametrize("n,trials", [(6, 400000), (7, 400000), (8, 300000), (10, 200000), (16, 60000)])
+def test_table3_monte_carlo_gpu(pf3, n, trials):
+    from paper_2407_20205_gb300 import montecarlo
+    table = montecarlo.paper_table()
+    z, o, t = montecarlo.estimate(n, trials)
+    assert z + o + t == trials
+    p = table[n]
+    sd = math.sqrt(p * (1 - p) / trials)
+    assert abs(z / trials - p) < 4.5 * sd
+    assert abs(o - t) < 5 * math.sqrt(trials)
