@@ -196,7 +196,9 @@ const void* batch_kernel_ptr(int v)
     case 0: return (const void*)batch_kernel<W, kBatchVariants[0].U, kBatchVariants[0].min_ctas>;
     case 1: return (const void*)batch_kernel<W, kBatchVariants[1].U, kBatchVariants[1].min_ctas>;
     case 2: return (const void*)batch_kernel<W, kBatchVariants[2].U, kBatchVariants[2].min_ctas>;
-    default: return (const void*)batch_kernel<W, kBatchVariants[3].U, kBatchVariants[3].min_ctas>;
+    case 3: return (const void*)batch_kernel<W, kBatchVariants[3].U, kBatchVariants[3].min_ctas>;
+    case 4: return (const void*)batch_kernel<W, kBatchVariants[4].U, kBatchVariants[4].min_ctas>;
+    default: return (const void*)batch_kernel<W, kBatchVariants[5].U, kBatchVariants[5].min_ctas>;
     }
 }
 

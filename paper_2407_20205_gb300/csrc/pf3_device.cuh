@@ -190,30 +190,26 @@ __device__ __noinline__ void walk_generic(const RowTable<W>& tab, int n, uint64_
 
 // ---------------------------------------------------------------------------
 // Grouped walk.  The Gray indices are cut into groups of 2^G consecutive
-// indices.  Only the first state of each group (the "base") is carried in
-// full (all W words of mag and sgn).  The other 2^G - 1 states of the group
-// differ from the base by a sum of rows 0..G-1 whose signs are fixed by the
-// index inside the group and the group's parity, so each is evaluated as a
-// "probe": base + C_j, computing only the low mag word (two LOP3) for the
-// zero test of Sec. 3.  A probe whose low 32 columns are all nonzero marks the
-// group; marked groups are replayed exactly (all words, sign from the
-// popcount of sgn) from the saved base.  The base moves to the next group by
-// one row-step with a combined constant (the group's net change of row G-1
-// plus the next group's first flip).
+// indices (group k = indices k*2^G .. k*2^G + 2^G - 1).  Only one state per
+// group (the "base") is carried in full (all W words of mag and sgn); the
+// other 2^G - 1 states of the group are evaluated as "probes" that compute
+// only the low mag word (two LOP3) for the zero test of Sec. 3.  A probe whose
+// low 32 columns are all nonzero marks the group; marked groups are replayed
+// exactly (all words, sign from the popcount of sgn) from the saved base.
 //
 // Index facts used (reflected binary code, gray(i) = i ^ (i >> 1)):
-//  * for a base i = k * 2^G, the low G bits of gray(i) are (k & 1) << (G-1);
-//  * for i + j (0 < j < 2^G) they are gray(j) ^ ((k & 1) << (G-1)), so
-//    relative to the base, row r < G-1 is present (added) iff bit r of
-//    gray(j) is set, and row G-1 is present iff j >= 2^(G-1), added when k is
-//    even and subtracted when k is odd;
-//  * over one group the net change is row G-1 only (+ for even k, - for odd);
-//  * the flip entering group k+1 is row t = G + tz(k+1), subtracted iff bit
-//    t+1 of the index (k+1) * 2^G is set.
+//  * inside group k the bits >= G of gray(i) are gray(k), and the low G bits
+//    are gray(j) ^ ((k & 1) << (G-1)) for i = k*2^G + j;
+//  * so the base of an even group is its first state (j = 0) and the base of
+//    an odd group its last state (j = 2^G - 1): in both cases the base's low G
+//    bits are 0, and the group's 2^G states are exactly base + (sum of the
+//    rows in s) for the 2^G subsets s of rows 0..G-1, all ADDED;
+//  * consecutive bases differ in one row only: row t = G + tz(k+1), the flip
+//    at index (k+1)*2^G, subtracted iff bit t+1 of that index is set.
 // Groups are unrolled 2^(U-G) at a time ("block" of 2^U indices); inside a
 // block every row, sign and mask is a compile-time choice except the flip of
 // row U-1 in the middle of the block (sign = parity of the block index) and
-// the flip that enters the next block (row U + tz(B+1), from the row table).
+// the flip into the next block (row U + tz(B+1), from the row table).
 // ---------------------------------------------------------------------------
 
 __host__ __device__ constexpr int ctz_const(int x)
@@ -221,29 +217,11 @@ __host__ __device__ constexpr int ctz_const(int x)
     return (x & 1) ? 0 : 1 + ctz_const(x >> 1);
 }
 
-__host__ __device__ constexpr int gray_const(int j)
-{
-    return j ^ (j >> 1);
-}
-
-template <int G>
-__host__ __device__ constexpr int probe_combos()
-{
-    return ((1 << (G - 1)) - 1) + 2 * (1 << (G - 1));
-}
-
-// probe j (1 <= j < 2^G) of a group with parity p -> its constant's slot
-template <int G>
-__host__ __device__ constexpr int probe_id(int j, int p)
-{
-    return j < (1 << (G - 1)) ? j - 1 : ((1 << (G - 1)) - 1) + 2 * (j - (1 << (G - 1))) + p;
-}
-
 // masks (K1 = [c == 0], K2 = [c == 1]) of the per-column constant
-// c = sum of rows in `plus` - sum of rows in `minus`
+// c = sum of the rows in `rows`
 template <int W>
-__device__ __forceinline__ void combo_masks(const RowTable<W>& tab, uint64_t plus, uint64_t minus,
-                                            uint32_t (&k1)[W], uint32_t (&k2)[W])
+__device__ __forceinline__ void subset_masks(const RowTable<W>& tab, uint64_t rows, uint32_t (&k1)[W],
+                                             uint32_t (&k2)[W])
 {
     State<W> c;
 #pragma unroll
@@ -251,13 +229,9 @@ __device__ __forceinline__ void combo_masks(const RowTable<W>& tab, uint64_t plu
         c.m[w] = 0u;
         c.s[w] = 0u;
     }
-    while (plus) {
-        add_row<W>(c, tab, 0, __ffsll((long long)plus) - 1);
-        plus &= plus - 1;
-    }
-    while (minus) {
-        add_row<W>(c, tab, 1, __ffsll((long long)minus) - 1);
-        minus &= minus - 1;
+    while (rows) {
+        add_row<W>(c, tab, 0, __ffsll((long long)rows) - 1);
+        rows &= rows - 1;
     }
 #pragma unroll
     for (int w = 0; w < W; ++w) {
@@ -266,66 +240,48 @@ __device__ __forceinline__ void combo_masks(const RowTable<W>& tab, uint64_t plu
     }
 }
 
-// Per-thread registers of the grouped walk: probe masks (low word only) and
-// the masks of the in-block group transitions (all words), slot
-// (t - G) * 2 + dir for row t and direction dir.
+// Per-thread registers of the grouped walk: probe masks for the 2^G - 1
+// nonzero subsets s of rows 0..G-1 (low word only, slot s - 1) and the row
+// masks of rows G..U-1 (all words) for the in-block base steps.
 template <int W, int G, int U>
 struct GroupRows {
-    static constexpr int kProbes = probe_combos<G>();
-    static constexpr int kTrans = 2 * (U - G);
+    static constexpr int kProbes = (1 << G) - 1;
+    static constexpr int kRows = U - G;
     uint32_t pk1[kProbes];
     uint32_t pk2[kProbes];
-    uint32_t dk1[kTrans][W];
-    uint32_t dk2[kTrans][W];
+    uint32_t rk1[kRows][W];
+    uint32_t rk2p[kRows][W];
+    uint32_t rk2m[kRows][W];
 };
 
 template <int W, int G, int U>
 __device__ __forceinline__ void load_group_rows(GroupRows<W, G, U>& R, const RowTable<W>& tab)
 {
-    constexpr int H = 1 << (G - 1);
 #pragma unroll
-    for (int j = 1; j < (1 << G); ++j) {
-#pragma unroll
-        for (int p = 0; p < 2; ++p) {
-            if (j < H && p == 1) continue;
-            const uint64_t low = (uint64_t)(gray_const(j) & (H - 1));
-            uint64_t plus = low, minus = 0;
-            if (j >= H) {
-                if (p == 0) plus |= 1ull << (G - 1);
-                else minus |= 1ull << (G - 1);
-            }
-            uint32_t k1[W], k2[W];
-            combo_masks<W>(tab, plus, minus, k1, k2);
-            R.pk1[probe_id<G>(j, p)] = k1[0];
-            R.pk2[probe_id<G>(j, p)] = k2[0];
-        }
+    for (int sub = 1; sub < (1 << G); ++sub) {
+        uint32_t k1[W], k2[W];
+        subset_masks<W>(tab, (uint64_t)sub, k1, k2);
+        R.pk1[sub - 1] = k1[0];
+        R.pk2[sub - 1] = k2[0];
     }
 #pragma unroll
     for (int t = G; t < U; ++t) {
 #pragma unroll
-        for (int dir = 0; dir < 2; ++dir) {
-            // entering a group after an even one (t == G) the finished group
-            // added row G-1; after an odd one (t > G) it subtracted it
-            uint64_t plus = 0, minus = 0;
-            if (t == G) plus |= 1ull << (G - 1);
-            else minus |= 1ull << (G - 1);
-            if (dir == 0) plus |= 1ull << t;
-            else minus |= 1ull << t;
-            uint32_t k1[W], k2[W];
-            combo_masks<W>(tab, plus, minus, k1, k2);
-#pragma unroll
-            for (int w = 0; w < W; ++w) {
-                R.dk1[(t - G) * 2 + dir][w] = k1[w];
-                R.dk2[(t - G) * 2 + dir][w] = k2[w];
-            }
+        for (int w = 0; w < W; ++w) {
+            R.rk1[t - G][w] = tab.e[0][t].k1[w];
+            R.rk2p[t - G][w] = tab.e[0][t].k2[w];
+            R.rk2m[t - G][w] = tab.e[1][t].k2[w];
         }
     }
 }
 
-// Exact terms of the group of 2^G indices starting at i0, from its base state.
+// Exact terms of group k (indices i0 .. i0 + 2^G - 1, i0 = k * 2^G) from its
+// base (first state for even k, last state for odd k).
 template <int W, int G>
 __device__ __noinline__ void replay_group(const RowTable<W>& tab, State<W> st, uint64_t i0, Counts& c)
 {
+    // for odd k the first state has row G-1 present where the base has not
+    if ((i0 >> G) & 1u) add_row<W>(st, tab, 0, G - 1);
     for (uint32_t j = 0; j < (1u << G); ++j) {
         const uint64_t i = i0 + j;
         if (j) {
@@ -405,19 +361,16 @@ __device__ __forceinline__ void queue_drain(WarpQueue<W>& q, const RowTable<W>& 
 template <int W, int G, int U, int GI>
 struct GroupSteps {
     static __device__ __forceinline__ void run(State<W>& st, const GroupRows<W, G, U>& R,
-                                               const uint32_t (&kmid1)[W], const uint32_t (&kmid2)[W],
-                                               uint64_t ibase, WarpQueue<W>& q, const RowTable<W>& tab,
-                                               Counts& c)
+                                               const uint32_t (&kmid2)[W], uint64_t ibase, WarpQueue<W>& q,
+                                               const RowTable<W>& tab, Counts& c)
     {
-        GroupSteps<W, G, U, GI - 1>::run(st, R, kmid1, kmid2, ibase, q, tab, c);
-        constexpr int g = GI - 1;            // group inside the block
-        constexpr int p = g & 1;             // its parity
+        GroupSteps<W, G, U, GI - 1>::run(st, R, kmid2, ibase, q, tab, c);
+        constexpr int g = GI - 1;  // group inside the block
         bool hit = (st.m[0] == 0xFFFFFFFFu);
 #pragma unroll
-        for (int j = 1; j < (1 << G); ++j) {
-            const int id = probe_id<G>(j, p);
-            const uint32_t gq = lop3<kLutG>(st.s[0], R.pk1[id], R.pk2[id]);
-            const uint32_t mq = lop3<kLutMag>(st.m[0], R.pk1[id], gq);
+        for (int sub = 1; sub < (1 << G); ++sub) {
+            const uint32_t gq = lop3<kLutG>(st.s[0], R.pk1[sub - 1], R.pk2[sub - 1]);
+            const uint32_t mq = lop3<kLutMag>(st.m[0], R.pk1[sub - 1], gq);
             hit |= (mq == 0xFFFFFFFFu);
         }
         if (hit)
@@ -425,11 +378,10 @@ struct GroupSteps {
         if (g + 1 < (1 << (U - G))) {
             constexpr int t = G + ctz_const(g + 1);
             constexpr int dir = ((g + 1) >> (t + 1 - G)) & 1;
-            if (t == U - 1) {
-                add_masks<W>(st, kmid1, kmid2);
-            } else {
-                constexpr int id = (t - G) * 2 + dir;
-                add_masks<W>(st, R.dk1[id], R.dk2[id]);
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                const uint32_t k2 = (t == U - 1) ? kmid2[w] : (dir ? R.rk2m[t - G][w] : R.rk2p[t - G][w]);
+                add_word(st.m[w], st.s[w], R.rk1[t - G][w], k2);
             }
         }
     }
@@ -437,9 +389,8 @@ struct GroupSteps {
 
 template <int W, int G, int U>
 struct GroupSteps<W, G, U, 0> {
-    static __device__ __forceinline__ void run(State<W>&, const GroupRows<W, G, U>&, const uint32_t (&)[W],
-                                               const uint32_t (&)[W], uint64_t, WarpQueue<W>&,
-                                               const RowTable<W>&, Counts&)
+    static __device__ __forceinline__ void run(State<W>&, const GroupRows<W, G, U>&, const uint32_t (&)[W], uint64_t,
+                                               WarpQueue<W>&, const RowTable<W>&, Counts&)
     {
     }
 };
@@ -454,21 +405,17 @@ __device__ __forceinline__ void walk_groups(const RowTable<W>& tab, const GroupR
 {
     State<W> st = initial_state<W>(n);
     if (len) st = seed_state<W>(tab, n, B0 << U);
-    constexpr int mid = (U - 1 - G) * 2;  // slot of the row U-1 transition
     for (uint64_t it = 0; it < trip; ++it) {
         if (it < len) {
             const uint64_t B = B0 + it;
-            uint32_t kmid1[W], kmid2[W];
+            // row U-1 flips mid-block: subtracted in odd blocks
+            uint32_t kmid2[W];
 #pragma unroll
-            for (int w = 0; w < W; ++w) {
-                kmid1[w] = (B & 1u) ? R.dk1[mid + 1][w] : R.dk1[mid][w];
-                kmid2[w] = (B & 1u) ? R.dk2[mid + 1][w] : R.dk2[mid][w];
-            }
-            GroupSteps<W, G, U, (1 << (U - G))>::run(st, R, kmid1, kmid2, B << U, q, tab, c);
+            for (int w = 0; w < W; ++w) kmid2[w] = (B & 1u) ? R.rk2m[U - 1 - G][w] : R.rk2p[U - 1 - G][w];
+            GroupSteps<W, G, U, (1 << (U - G))>::run(st, R, kmid2, B << U, q, tab, c);
             if (it + 1 < len) {
-                // the block's last group (odd) subtracted row G-1 on the way;
-                // then the flip into block B+1
-                add_row<W>(st, tab, 1, G - 1);
+                // the flip into block B+1 (the block's last group is odd, its
+                // base already sits at the block's last index)
                 const uint64_t nb = B + 1;
                 const int z = __ffsll((long long)nb) - 1;
                 add_row<W>(st, tab, (int)((nb >> (z + 1)) & 1u), U + z);

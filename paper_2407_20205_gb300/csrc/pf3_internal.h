@@ -17,10 +17,11 @@ struct KernelVariant {
     int U;
     int min_ctas;
 };
-constexpr int kNumSingleVariants = 5;
-constexpr KernelVariant kSingleVariants[kNumSingleVariants] = {{8, 2}, {7, 2}, {8, 1}, {9, 1}, {9, 2}};
-constexpr int kNumBatchVariants = 4;
-constexpr KernelVariant kBatchVariants[kNumBatchVariants] = {{8, 4}, {7, 4}, {8, 2}, {9, 2}};
+constexpr int kNumSingleVariants = 7;
+constexpr KernelVariant kSingleVariants[kNumSingleVariants] = {{8, 2}, {7, 2}, {9, 2}, {10, 2}, {9, 1},
+                                                               {10, 1}, {8, 3}};
+constexpr int kNumBatchVariants = 6;
+constexpr KernelVariant kBatchVariants[kNumBatchVariants] = {{8, 4}, {7, 4}, {9, 4}, {9, 2}, {10, 2}, {8, 6}};
 
 // One range job for the single-matrix kernel; all indices are Gray indices.
 struct SingleArgs {

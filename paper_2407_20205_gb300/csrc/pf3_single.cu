@@ -152,7 +152,9 @@ const void* single_kernel_ptr(int v)
     case 1: return (const void*)single_kernel<W, kSingleVariants[1].U, kSingleVariants[1].min_ctas>;
     case 2: return (const void*)single_kernel<W, kSingleVariants[2].U, kSingleVariants[2].min_ctas>;
     case 3: return (const void*)single_kernel<W, kSingleVariants[3].U, kSingleVariants[3].min_ctas>;
-    default: return (const void*)single_kernel<W, kSingleVariants[4].U, kSingleVariants[4].min_ctas>;
+    case 4: return (const void*)single_kernel<W, kSingleVariants[4].U, kSingleVariants[4].min_ctas>;
+    case 5: return (const void*)single_kernel<W, kSingleVariants[5].U, kSingleVariants[5].min_ctas>;
+    default: return (const void*)single_kernel<W, kSingleVariants[6].U, kSingleVariants[6].min_ctas>;
     }
 }
 
