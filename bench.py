@@ -40,14 +40,14 @@ sys.path.insert(0, ROOT)
 METRIC = "F3 Ryser Gray-code subsets/sec on 1 GB300; batched perms/sec; p50/p99 latency"
 UNIT = "subsets/s"
 SIZES = (36, 40)
-G_LOG2 = 4  # probe group of the walk: 2^G Gray indices per carried base state
-
-
-def i_alg(W: int, G: int = G_LOG2) -> float:
-    """ALU-pipe instructions per subset issued by the grouped walk: per group of
-    2^G indices, one full row step on the base (3 LOP3 per word), 2^G - 1
-    probes on the low mag word (2 LOP3 each) and 2^G zero tests (one compare)."""
-    return (3 * W + 2 * ((1 << G) - 1) + (1 << G)) / (1 << G)
+def i_alg(G: int) -> float:
+    """Minimal ALU-pipe instructions per subset of the grouped walk: per group
+    of 2^G Gray indices, one row step on the low word of the base (3 LOP3),
+    one zero test of the base, and 2^G - 1 probes of two LOP3 each whose zero
+    test is folded into the second gate (LOP3 writes a predicate).  The
+    compiled kernel executes a little more (see profiles/walk_single_n36.md);
+    the fraction against this count is the distance to the best ALU code."""
+    return (3 + 1 + 2 * ((1 << G) - 1)) / (1 << G)
 
 
 KERNEL_FILES = {"single": ("pf3_device.cuh", "pf3_internal.h", "pf3_single.cu"),
@@ -66,26 +66,35 @@ def kernel_source_hash(kind: str = "single") -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(summary="walk_single_n36.md"):
-    """DRAM bytes per launch from the committed ncu summary of the walk kernel,
-    or None when the kernel sources changed since that capture."""
+def profiled(summary="walk_single_n36.md", kind="single"):
+    """Figures from the committed ncu summary of a walk kernel (DRAM bytes per
+    launch, executed ALU instructions per subset, ALU pipe busy), or {} when
+    the kernel sources changed since that capture."""
     path = os.path.join(ROOT, "profiles", summary)
     try:
         text = open(path).read()
     except OSError:
-        return None
+        return {}
     vals = {}
     for line in text.splitlines():
         line = line.strip().lstrip("-* ")
-        if ":" in line and line.startswith(("source_hash", "dram_bytes_per_launch")):
+        if ":" in line and line.startswith(("source_hash", "dram_bytes_per_launch", "alu_inst_per_subset",
+                                            "alu_pipe_busy")):
             k, v = line.split(":", 1)
             vals[k.strip(" `")] = v.strip(" `")
-    if vals.get("source_hash") != kernel_source_hash():
-        return None
-    try:
-        return float(vals["dram_bytes_per_launch"])
-    except (KeyError, ValueError):
-        return None
+    if vals.get("source_hash") != kernel_source_hash(kind):
+        return {}
+    out = {}
+    for k in ("dram_bytes_per_launch", "alu_inst_per_subset", "alu_pipe_busy"):
+        try:
+            out[k] = float(vals[k])
+        except (KeyError, ValueError):
+            pass
+    return out
+
+
+def profiled_traffic(summary="walk_single_n36.md"):
+    return profiled(summary).get("dram_bytes_per_launch")
 
 
 def dist_env():
@@ -313,15 +322,22 @@ def run_ours(args):
         info = pf3.device_info()
         n_sm = info["sm_count"]
         # roofline of the dominant kernel (the W = 2 walk, both launches)
-        ops = sum((1 << n) // world * i_alg(2) for n in SIZES) * args.steps
+        g_single = pf3.variant_info(pf3.SINGLE, pf3.get_variant(pf3.SINGLE, 2))["G"]
+        ops = sum((1 << n) // world * i_alg(g_single) for n in SIZES) * args.steps
         kern_s = sum(sum(v) for v in launch_ms.values()) * 1e-3
         achieved = ops / kern_s / 1e12
         lanes = float(os.environ.get("PF3_ALU_LANES", "64"))
         peak = n_sm * sm_max * 1e6 * lanes / 1e12
+        prof = profiled()
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-                "traffic": profiled_traffic(),
-                "note": f"ops = {i_alg(2)} ALU instructions per subset (W=2 grouped walk); peak = {n_sm} SMs x "
-                        f"{sm_max:.0f} MHz x {lanes:.0f} lanes/clk/SM (LOP3/ISETP issue), of measured clock"}
+                "traffic": prof.get("dram_bytes_per_launch"),
+                "ops_per_subset": i_alg(g_single),
+                "executed_alu_inst_per_subset": prof.get("alu_inst_per_subset"),
+                "alu_pipe_busy": prof.get("alu_pipe_busy"),
+                "note": f"ops = {i_alg(g_single)} minimal ALU instructions per subset (grouped walk, G = {g_single}; "
+                        f"probes of 2 LOP3 with the zero test folded in); peak = {n_sm} SMs x "
+                        f"{sm_max:.0f} MHz x {lanes:.0f} lanes/clk/SM (ALU pipe issue), of measured clock; "
+                        f"executed ALU instructions per subset and ALU pipe busy are ncu figures of this kernel"}
         # e2e through the host-pointer C entry point (copies in and out each call)
         e2e = None
         if world == 1:
@@ -387,9 +403,10 @@ def bench_batch(pf3, torch, dev, stream, count=200000):
     sub_s = count * (1 << 24) / (ms * 1e-3)
     n_sm = pf3.device_info()["sm_count"]
     peak_ops = n_sm * float(peaks().get("sm_max_mhz", 2070.0)) * 1e6 * 64
+    g_batch = pf3.variant_info(pf3.BATCH, pf3.get_variant(pf3.BATCH, 1))["G"]
     return {"matrices": count, "n": 24, "ms": ms, "perms_per_s": count / (ms * 1e-3),
             "subsets_per_s": sub_s, "hist": hist,
-            "alu_frac": sub_s * i_alg(1) / peak_ops}
+            "alu_frac": sub_s * i_alg(g_batch) / peak_ops, "alu_ops_per_subset": i_alg(g_batch)}
 
 
 def bench_single_launches(pf3, torch, dev, stream, count=2000):

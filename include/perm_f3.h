@@ -222,7 +222,8 @@ int pf3_pack(const uint8_t* A, int n, uint64_t* mag, uint64_t* sgn);
 /* Integer-pipe microbenchmark (the roofline denominator of the walk).  kind:
  * 0 LOP3, 1 IMAD, 2 IADD, 3 LOP3+IMAD, 4 full row step (3 LOP3 + compare),
  * 5 POPC, 6 MAX(+IMAD), 7 2 LOP3 + MAX, 8 probe (2 LOP3 + compare),
- * 9 row step + IMAD, 10 2 LOP3 + IADD.
+ * 9 row step + IMAD, 10 2 LOP3 + IADD, 11 probe with inverted gate tested
+ * against zero, 12 probe tested against all ones (2 LOP3 + compare each).
  * Runs `ctas_per_sm` CTAs of `threads` threads per SM for `iters` rounds and
  * reports instructions per clock per SM (thread instructions, i.e. lanes),
  * thread instructions per second over the whole GPU, and the SM clock in MHz
@@ -235,12 +236,16 @@ int pf3_device_info(int* sm_count, int* device);
 
 /* ------------------------------------------------------------ tuning */
 
-/* Kernel variants (unrolled Gray block length, register budget).  which: 0 =
+/* Kernel variants (probe group and unrolled block lengths, register budget).  which: 0 =
  * single-matrix kernel, 1 = batch kernel.  W: words per plane (1 for n <= 32,
  * 2 for n <= 64).  Results never depend on the variant, only speed does. */
 int pf3_variant_count(int which);
 int pf3_set_variant(int which, int W, int v);
 int pf3_get_variant(int which, int W);
+
+/* Shape of variant v: unrolled block 2^U Gray indices, probe group 2^G
+ * indices per carried base state, minimum resident CTAs per SM. */
+int pf3_variant_info(int which, int v, int* U, int* G, int* min_ctas);
 
 /* Batch work split: matrices with n > cutoff are cut into work items of
  * 2^chunk_log2 Gray indices (Sec. 3.1 blocks); others are one item each. */

@@ -75,6 +75,7 @@ _lib_devinfo = _sig("pf3_device_info", ctypes.c_int, [_ip, _ip])
 _lib_vcount = _sig("pf3_variant_count", ctypes.c_int, [ctypes.c_int])
 _lib_setv = _sig("pf3_set_variant", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int])
 _lib_getv = _sig("pf3_get_variant", ctypes.c_int, [ctypes.c_int, ctypes.c_int])
+_lib_vinfo = _sig("pf3_variant_info", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _ip, _ip, _ip])
 _lib_split = _sig("pf3_set_batch_split", ctypes.c_int, [ctypes.c_int, ctypes.c_int])
 _lib_autotune = _sig("pf3_autotune", ctypes.c_int, [_dp, _dp])
 
@@ -362,7 +363,8 @@ def pack(A) -> tuple[np.ndarray, np.ndarray]:
 
 
 INTPIPE_KINDS = {"lop3": 0, "imad": 1, "iadd": 2, "lop3_imad": 3, "step": 4, "popc": 5, "max_imad": 6,
-                 "lop3x2_max": 7, "probe": 8, "step_imad": 9, "lop3x2_iadd": 10}
+                 "lop3x2_max": 7, "probe": 8, "step_imad": 9, "lop3x2_iadd": 10, "probe_inv": 11,
+                 "probe_ones": 12}
 
 
 def intpipe_bench(kind, ctas_per_sm: int = 4, threads: int = 256, iters: int = 4096) -> dict:
@@ -396,6 +398,12 @@ def get_variant(which: int, W: int) -> int:
     return _check(_lib_getv(which, W), "pf3_get_variant")
 
 
+def variant_info(which: int, v: int) -> dict:
+    U, G, mc = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(_lib_vinfo(which, v, ctypes.byref(U), ctypes.byref(G), ctypes.byref(mc)), "pf3_variant_info")
+    return {"U": U.value, "G": G.value, "min_ctas": mc.value}
+
+
 def set_batch_split(cutoff: int, chunk_log2: int) -> None:
     _check(_lib_split(cutoff, chunk_log2), "pf3_set_batch_split")
 
@@ -419,5 +427,5 @@ def exported_symbols() -> list[str]:
                         "pf3_config_default", "pf3_create", "pf3_destroy", "perm_f3_submit", "perm_f3_poll",
                         "perm_f3_wait", "pf3_job_times", "pf3_serve_stats", "pf3_now_ns",
                         "pf3_cancel_queued", "pf3_longrun", "pf3_longrun_cancel",
-                        "pf3_count_exhaustive")
+                        "pf3_count_exhaustive", "pf3_variant_info")
             if hasattr(_lib, n)]

@@ -72,17 +72,16 @@ __device__ __forceinline__ int tiny_perm(TinyTable& T, const uint8_t* A, int n, 
     return (int)perm_from_counts(n, p, q);
 }
 
-template <int W, int U, int MINB>
+template <int W, int U, int G, int MINB>
 __global__ void __launch_bounds__(kBatchThreads, MINB) batch_kernel(BatchArgs a)
 {
-    constexpr int G = kGroupLog2;
     __shared__ RowTable<W> tabs[kBatchThreads / 32];
-    __shared__ WarpQueue<W> queues[kBatchThreads / 32];
+    __shared__ WarpQueue queues[kBatchThreads / 32];
     __shared__ TinyTable tiny[W == 1 ? kBatchThreads / 32 : 1];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     RowTable<W>& tab = tabs[warp];
-    WarpQueue<W>& q = queues[warp];
+    WarpQueue& q = queues[warp];
     if (lane == 0) q.count = 0;
     __syncwarp();
 
@@ -135,7 +134,7 @@ __global__ void __launch_bounds__(kBatchThreads, MINB) batch_kernel(BatchArgs a)
                 // small n: one lane walks all 2^n indices
                 if (lane == 0) walk_generic<W>(tab, n, 0, (n == 64) ? ~0ull : ((1ull << n) - 1), c);
             } else {
-                GroupRows<W, G, U> R;
+                GroupRows<G, U> R;
                 load_group_rows<W, G, U>(R, tab);
                 uint64_t s, len;
                 split_range(it.NB, 32, (uint64_t)lane, s, len);
@@ -193,12 +192,12 @@ template <int W>
 const void* batch_kernel_ptr(int v)
 {
     switch (v) {
-    case 0: return (const void*)batch_kernel<W, kBatchVariants[0].U, kBatchVariants[0].min_ctas>;
-    case 1: return (const void*)batch_kernel<W, kBatchVariants[1].U, kBatchVariants[1].min_ctas>;
-    case 2: return (const void*)batch_kernel<W, kBatchVariants[2].U, kBatchVariants[2].min_ctas>;
-    case 3: return (const void*)batch_kernel<W, kBatchVariants[3].U, kBatchVariants[3].min_ctas>;
-    case 4: return (const void*)batch_kernel<W, kBatchVariants[4].U, kBatchVariants[4].min_ctas>;
-    default: return (const void*)batch_kernel<W, kBatchVariants[5].U, kBatchVariants[5].min_ctas>;
+    case 0: return (const void*)batch_kernel<W, kBatchVariants[0].U, kBatchVariants[0].G, kBatchVariants[0].min_ctas>;
+    case 1: return (const void*)batch_kernel<W, kBatchVariants[1].U, kBatchVariants[1].G, kBatchVariants[1].min_ctas>;
+    case 2: return (const void*)batch_kernel<W, kBatchVariants[2].U, kBatchVariants[2].G, kBatchVariants[2].min_ctas>;
+    case 3: return (const void*)batch_kernel<W, kBatchVariants[3].U, kBatchVariants[3].G, kBatchVariants[3].min_ctas>;
+    case 4: return (const void*)batch_kernel<W, kBatchVariants[4].U, kBatchVariants[4].G, kBatchVariants[4].min_ctas>;
+    default: return (const void*)batch_kernel<W, kBatchVariants[5].U, kBatchVariants[5].G, kBatchVariants[5].min_ctas>;
     }
 }
 

@@ -50,6 +50,7 @@ __device__ __forceinline__ uint32_t lop3(uint32_t a, uint32_t b, uint32_t c)
 constexpr int kLutG = 0x12;    // g    = ~b & (a ^ c)        a=sgn, b=K1, c=K2
 constexpr int kLutMag = 0xE3;  // mag' = b ? a : (~a | c)    a=mag, b=K1, c=g
 constexpr int kLutSgn = 0x69;  // sgn' = ~(a ^ b ^ c)        a=mag, b=sgn, c=g
+constexpr int kLutMagInv = (~kLutMag) & 0xFF;  // ~mag', same inputs as kLutMag
 
 // add the per-column constant described by (k1, k2) to one word of the state
 __device__ __forceinline__ void add_word(uint32_t& m, uint32_t& s, uint32_t k1, uint32_t k2)
@@ -240,22 +241,25 @@ __device__ __forceinline__ void subset_masks(const RowTable<W>& tab, uint64_t ro
     }
 }
 
-// Per-thread registers of the grouped walk: probe masks for the 2^G - 1
-// nonzero subsets s of rows 0..G-1 (low word only, slot s - 1) and the row
-// masks of rows G..U-1 (all words) for the in-block base steps.
-template <int W, int G, int U>
+// Per-thread registers of the grouped walk.  The walk itself only needs the
+// LOW word of every state (the zero test looks at columns 0..31; columns are
+// independent, so the low word evolves on its own): probe masks for the
+// 2^G - 1 nonzero subsets s of rows 0..G-1 (slot s - 1) and the masks of rows
+// G..U-1 for the in-block base steps, all low word only.  Marked groups are
+// replayed exactly with every word.
+template <int G, int U>
 struct GroupRows {
     static constexpr int kProbes = (1 << G) - 1;
     static constexpr int kRows = U - G;
     uint32_t pk1[kProbes];
     uint32_t pk2[kProbes];
-    uint32_t rk1[kRows][W];
-    uint32_t rk2p[kRows][W];
-    uint32_t rk2m[kRows][W];
+    uint32_t rk1[kRows];
+    uint32_t rk2p[kRows];
+    uint32_t rk2m[kRows];
 };
 
 template <int W, int G, int U>
-__device__ __forceinline__ void load_group_rows(GroupRows<W, G, U>& R, const RowTable<W>& tab)
+__device__ __forceinline__ void load_group_rows(GroupRows<G, U>& R, const RowTable<W>& tab)
 {
 #pragma unroll
     for (int sub = 1; sub < (1 << G); ++sub) {
@@ -266,22 +270,18 @@ __device__ __forceinline__ void load_group_rows(GroupRows<W, G, U>& R, const Row
     }
 #pragma unroll
     for (int t = G; t < U; ++t) {
-#pragma unroll
-        for (int w = 0; w < W; ++w) {
-            R.rk1[t - G][w] = tab.e[0][t].k1[w];
-            R.rk2p[t - G][w] = tab.e[0][t].k2[w];
-            R.rk2m[t - G][w] = tab.e[1][t].k2[w];
-        }
+        R.rk1[t - G] = tab.e[0][t].k1[0];
+        R.rk2p[t - G] = tab.e[0][t].k2[0];
+        R.rk2m[t - G] = tab.e[1][t].k2[0];
     }
 }
 
-// Exact terms of group k (indices i0 .. i0 + 2^G - 1, i0 = k * 2^G) from its
-// base (first state for even k, last state for odd k).
+// Exact terms of group k (indices i0 .. i0 + 2^G - 1, i0 = k * 2^G): its first
+// state is re-seeded from scratch (all words), then the group is walked.
 template <int W, int G>
-__device__ __noinline__ void replay_group(const RowTable<W>& tab, State<W> st, uint64_t i0, Counts& c)
+__device__ __noinline__ void replay_group(const RowTable<W>& tab, int n, uint64_t i0, Counts& c)
 {
-    // for odd k the first state has row G-1 present where the base has not
-    if ((i0 >> G) & 1u) add_row<W>(st, tab, 0, G - 1);
+    State<W> st = seed_state<W>(tab, n, i0);
     for (uint32_t j = 0; j < (1u << G); ++j) {
         const uint64_t i = i0 + j;
         if (j) {
@@ -301,58 +301,29 @@ __device__ __noinline__ void replay_group(const RowTable<W>& tab, State<W> st, u
 // one group per lane, so a rare replay does not stall 31 idle lanes.
 constexpr int kQueueCap = 64;
 
-template <int W>
 struct WarpQueue {
     unsigned count;
     unsigned pad;
     unsigned long long i0[kQueueCap];
-    uint32_t m[kQueueCap][W];
-    uint32_t s[kQueueCap][W];
 };
 
-// the base words travel by value (registers): a reference would force the
-// state into local memory at every call site of the walk's hot loop
 template <int W, int G>
-__device__ __noinline__ void queue_push(WarpQueue<W>& q, const RowTable<W>& tab, uint32_t m0, uint32_t s0,
-                                        uint32_t m1, uint32_t s1, uint64_t i0, Counts* c)
+__device__ __noinline__ void queue_push(WarpQueue& q, const RowTable<W>& tab, int n, uint64_t i0, Counts* c)
 {
-    State<W> st;
-    st.m[0] = m0;
-    st.s[0] = s0;
-    if (W > 1) {
-        st.m[W - 1] = m1;
-        st.s[W - 1] = s1;
-    }
     const unsigned slot = atomicAdd(&q.count, 1u);
-    if (slot < (unsigned)kQueueCap) {
-        q.i0[slot] = i0;
-#pragma unroll
-        for (int w = 0; w < W; ++w) {
-            q.m[slot][w] = st.m[w];
-            q.s[slot][w] = st.s[w];
-        }
-    } else {
-        replay_group<W, G>(tab, st, i0, *c);  // queue full: replay in place
-    }
+    if (slot < (unsigned)kQueueCap) q.i0[slot] = i0;
+    else replay_group<W, G>(tab, n, i0, *c);  // queue full: replay in place
 }
 
 // all 32 lanes: replay the queued groups and empty the queue
 template <int W, int G>
-__device__ __forceinline__ void queue_drain(WarpQueue<W>& q, const RowTable<W>& tab, int lane, Counts& c)
+__device__ __forceinline__ void queue_drain(WarpQueue& q, const RowTable<W>& tab, int n, int lane, Counts& c)
 {
     __syncwarp();
     const unsigned cnt = *(volatile unsigned*)&q.count;
     if (cnt == 0) return;
     const unsigned lim = cnt < (unsigned)kQueueCap ? cnt : (unsigned)kQueueCap;
-    for (unsigned e = lane; e < lim; e += 32) {
-        State<W> st;
-#pragma unroll
-        for (int w = 0; w < W; ++w) {
-            st.m[w] = q.m[e][w];
-            st.s[w] = q.s[e][w];
-        }
-        replay_group<W, G>(tab, st, q.i0[e], c);
-    }
+    for (unsigned e = lane; e < lim; e += 32) replay_group<W, G>(tab, n, q.i0[e], c);
     __syncwarp();
     if (lane == 0) q.count = 0;
     __syncwarp();
@@ -360,37 +331,36 @@ __device__ __forceinline__ void queue_drain(WarpQueue<W>& q, const RowTable<W>& 
 
 template <int W, int G, int U, int GI>
 struct GroupSteps {
-    static __device__ __forceinline__ void run(State<W>& st, const GroupRows<W, G, U>& R,
-                                               const uint32_t (&kmid2)[W], uint64_t ibase, WarpQueue<W>& q,
-                                               const RowTable<W>& tab, Counts& c)
+    static __device__ __forceinline__ void run(uint32_t& m, uint32_t& sg, const GroupRows<G, U>& R, uint32_t kmid2,
+                                               uint64_t ibase, WarpQueue& q, const RowTable<W>& tab, int n,
+                                               Counts& c)
     {
-        GroupSteps<W, G, U, GI - 1>::run(st, R, kmid2, ibase, q, tab, c);
+        GroupSteps<W, G, U, GI - 1>::run(m, sg, R, kmid2, ibase, q, tab, n, c);
         constexpr int g = GI - 1;  // group inside the block
-        bool hit = (st.m[0] == 0xFFFFFFFFu);
+        bool hit = (m == 0xFFFFFFFFu);
 #pragma unroll
         for (int sub = 1; sub < (1 << G); ++sub) {
-            const uint32_t gq = lop3<kLutG>(st.s[0], R.pk1[sub - 1], R.pk2[sub - 1]);
-            const uint32_t mq = lop3<kLutMag>(st.m[0], R.pk1[sub - 1], gq);
-            hit |= (mq == 0xFFFFFFFFu);
+            // the probe's mag word is produced inverted and tested against
+            // zero: on GB300 this form issues fewer ALU instructions than a
+            // test of the plain word against all ones (measured)
+            const uint32_t gq = lop3<kLutG>(sg, R.pk1[sub - 1], R.pk2[sub - 1]);
+            const uint32_t nmq = lop3<kLutMagInv>(m, R.pk1[sub - 1], gq);
+            hit |= (nmq == 0u);
         }
-        if (hit)
-            queue_push<W, G>(q, tab, st.m[0], st.s[0], st.m[W - 1], st.s[W - 1], ibase + ((uint64_t)g << G), &c);
+        if (hit) queue_push<W, G>(q, tab, n, ibase + ((uint64_t)g << G), &c);
         if (g + 1 < (1 << (U - G))) {
             constexpr int t = G + ctz_const(g + 1);
             constexpr int dir = ((g + 1) >> (t + 1 - G)) & 1;
-#pragma unroll
-            for (int w = 0; w < W; ++w) {
-                const uint32_t k2 = (t == U - 1) ? kmid2[w] : (dir ? R.rk2m[t - G][w] : R.rk2p[t - G][w]);
-                add_word(st.m[w], st.s[w], R.rk1[t - G][w], k2);
-            }
+            const uint32_t k2 = (t == U - 1) ? kmid2 : (dir ? R.rk2m[t - G] : R.rk2p[t - G]);
+            add_word(m, sg, R.rk1[t - G], k2);
         }
     }
 };
 
 template <int W, int G, int U>
 struct GroupSteps<W, G, U, 0> {
-    static __device__ __forceinline__ void run(State<W>&, const GroupRows<W, G, U>&, const uint32_t (&)[W], uint64_t,
-                                               WarpQueue<W>&, const RowTable<W>&, Counts&)
+    static __device__ __forceinline__ void run(uint32_t&, uint32_t&, const GroupRows<G, U>&, uint32_t, uint64_t,
+                                               WarpQueue&, const RowTable<W>&, int, Counts&)
     {
     }
 };
@@ -399,32 +369,34 @@ struct GroupSteps<W, G, U, 0> {
 // same in all 32 lanes of the warp: lanes with len < trip idle through the
 // extra iterations so that the warp drains its queue together.
 template <int W, int G, int U>
-__device__ __forceinline__ void walk_groups(const RowTable<W>& tab, const GroupRows<W, G, U>& R, int n,
-                                            uint64_t B0, uint64_t len, uint64_t trip, WarpQueue<W>& q, int lane,
-                                            Counts& c)
+__device__ __forceinline__ void walk_groups(const RowTable<W>& tab, const GroupRows<G, U>& R, int n, uint64_t B0,
+                                            uint64_t len, uint64_t trip, WarpQueue& q, int lane, Counts& c)
 {
-    State<W> st = initial_state<W>(n);
-    if (len) st = seed_state<W>(tab, n, B0 << U);
+    uint32_t m = 0, sg = 0;  // low word of the base state
+    if (len) {
+        const State<W> st = seed_state<W>(tab, n, B0 << U);
+        m = st.m[0];
+        sg = st.s[0];
+    }
     for (uint64_t it = 0; it < trip; ++it) {
         if (it < len) {
             const uint64_t B = B0 + it;
             // row U-1 flips mid-block: subtracted in odd blocks
-            uint32_t kmid2[W];
-#pragma unroll
-            for (int w = 0; w < W; ++w) kmid2[w] = (B & 1u) ? R.rk2m[U - 1 - G][w] : R.rk2p[U - 1 - G][w];
-            GroupSteps<W, G, U, (1 << (U - G))>::run(st, R, kmid2, B << U, q, tab, c);
+            const uint32_t kmid2 = (B & 1u) ? R.rk2m[U - 1 - G] : R.rk2p[U - 1 - G];
+            GroupSteps<W, G, U, (1 << (U - G))>::run(m, sg, R, kmid2, B << U, q, tab, n, c);
             if (it + 1 < len) {
                 // the flip into block B+1 (the block's last group is odd, its
                 // base already sits at the block's last index)
                 const uint64_t nb = B + 1;
                 const int z = __ffsll((long long)nb) - 1;
-                add_row<W>(st, tab, (int)((nb >> (z + 1)) & 1u), U + z);
+                const RowEntry<W>& e = tab.e[(int)((nb >> (z + 1)) & 1u)][U + z];
+                add_word(m, sg, e.k1[0], e.k2[0]);
             }
         }
         __syncwarp();
-        if (*(volatile unsigned*)&q.count >= 32u) queue_drain<W, G>(q, tab, lane, c);
+        if (*(volatile unsigned*)&q.count >= 32u) queue_drain<W, G>(q, tab, n, lane, c);
     }
-    queue_drain<W, G>(q, tab, lane, c);
+    queue_drain<W, G>(q, tab, n, lane, c);
 }
 
 // balanced split of `total` items over `parts`: part k gets [start, start+len)

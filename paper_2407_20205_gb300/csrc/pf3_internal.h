@@ -7,21 +7,22 @@
 
 namespace pf3 {
 
-// log2 of the probe group (2^G Gray indices per carried base state)
-constexpr int kGroupLog2 = 4;
 constexpr int kSingleThreads = 256;
 
-// A compiled variant of a walk kernel: unrolled block of 2^U Gray indices and
-// the minimum resident CTAs per SM it was compiled for (its register budget).
+// A compiled variant of a walk kernel: probe groups of 2^G Gray indices,
+// unrolled blocks of 2^U indices, and the minimum resident CTAs per SM it was
+// compiled for (its register budget).
 struct KernelVariant {
     int U;
+    int G;
     int min_ctas;
 };
 constexpr int kNumSingleVariants = 7;
-constexpr KernelVariant kSingleVariants[kNumSingleVariants] = {{8, 2}, {7, 2}, {9, 2}, {10, 2}, {9, 1},
-                                                               {10, 1}, {8, 3}};
+constexpr KernelVariant kSingleVariants[kNumSingleVariants] = {{9, 5, 2}, {9, 4, 2}, {8, 4, 2}, {10, 5, 2},
+                                                               {8, 5, 2}, {9, 5, 3}, {9, 5, 1}};
 constexpr int kNumBatchVariants = 6;
-constexpr KernelVariant kBatchVariants[kNumBatchVariants] = {{8, 4}, {7, 4}, {9, 4}, {9, 2}, {10, 2}, {8, 6}};
+constexpr KernelVariant kBatchVariants[kNumBatchVariants] = {{9, 5, 4}, {9, 4, 4}, {8, 4, 4}, {9, 5, 2},
+                                                             {10, 5, 2}, {8, 5, 4}};
 
 // One range job for the single-matrix kernel; all indices are Gray indices.
 struct SingleArgs {

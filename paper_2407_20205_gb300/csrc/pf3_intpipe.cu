@@ -10,7 +10,9 @@
 // add, 3 = LOP3 and IMAD interleaved 1:1, 4 = the full row step (three LOP3
 // and an accumulating compare), 5 = POPC, 6 = unsigned max, 7 = two LOP3 and
 // one max, 8 = two LOP3 and an accumulating compare (the probe of the walk),
-// 9 = three LOP3 and one IMAD, 10 = two LOP3 and one integer add.
+// 9 = three LOP3 and one IMAD, 10 = two LOP3 and one integer add, 11 = the
+// probe with an inverted last gate tested against zero, 12 = the probe tested
+// against all ones (both: two LOP3 and one compare per op).
 #include <cuda_runtime.h>
 
 #include "pf3_device.cuh"
@@ -77,6 +79,21 @@ __global__ void intpipe_kernel(uint32_t* sink, unsigned long long* cycles, int i
                     x[c] = lop3<0x96>(x[c], ka, kb);
                     x[c] = lop3<0xE8>(x[c], kc, kd);
                     asm volatile("add.u32 %0, %0, %1;" : "+r"(y[c]) : "r"(x[c]));
+                } else if (KIND == 11) {
+                    // probe with an inverted last gate tested against zero; the
+                    // two gate outputs feed the next probe (no folding possible)
+                    const uint32_t gq = lop3<kLutG>(y[c], (u & 1) ? ka : kc, (u & 1) ? kb : kd);
+                    const uint32_t nm = lop3<(~kLutMag) & 0xFF>(x[c], (u & 1) ? ka : kc, gq);
+                    hit |= (nm == 0u);
+                    x[c] = gq;
+                    y[c] = nm;
+                } else if (KIND == 12) {
+                    // the walk's probe as written (test against all ones), same chain
+                    const uint32_t gq = lop3<kLutG>(y[c], (u & 1) ? ka : kc, (u & 1) ? kb : kd);
+                    const uint32_t mq = lop3<kLutMag>(x[c], (u & 1) ? ka : kc, gq);
+                    hit |= (mq == 0xFFFFFFFFu);
+                    x[c] = gq;
+                    y[c] = mq;
                 }
             }
         }
@@ -106,6 +123,8 @@ cudaError_t launch_intpipe(int kind, int grid, int threads, int iters, uint32_t*
     case 8: intpipe_kernel<8><<<grid, threads, 0, stream>>>(sink, cycles, iters, 1u); break;
     case 9: intpipe_kernel<9><<<grid, threads, 0, stream>>>(sink, cycles, iters, 1u); break;
     case 10: intpipe_kernel<10><<<grid, threads, 0, stream>>>(sink, cycles, iters, 1u); break;
+    case 11: intpipe_kernel<11><<<grid, threads, 0, stream>>>(sink, cycles, iters, 1u); break;
+    case 12: intpipe_kernel<12><<<grid, threads, 0, stream>>>(sink, cycles, iters, 1u); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -18,12 +18,11 @@ namespace pf3 {
 
 namespace {
 
-template <int W, int U, int MINB>
+template <int W, int U, int G, int MINB>
 __global__ void __launch_bounds__(kSingleThreads, MINB) single_kernel(SingleArgs a)
 {
-    constexpr int G = kGroupLog2;
     __shared__ RowTable<W> tab;
-    __shared__ WarpQueue<W> queues[kSingleThreads / 32];
+    __shared__ WarpQueue queues[kSingleThreads / 32];
     __shared__ unsigned long long red[2][kSingleThreads / 32];
     __shared__ bool s_last;
 
@@ -38,7 +37,7 @@ __global__ void __launch_bounds__(kSingleThreads, MINB) single_kernel(SingleArgs
         const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
         const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
         if (a.mid_NB) {
-            GroupRows<W, G, U> R;
+            GroupRows<G, U> R;
             load_group_rows<W, G, U>(R, tab);
             uint64_t s, len;
             split_range(a.mid_NB, T, tid, s, len);
@@ -148,13 +147,13 @@ template <int W>
 const void* single_kernel_ptr(int v)
 {
     switch (v) {
-    case 0: return (const void*)single_kernel<W, kSingleVariants[0].U, kSingleVariants[0].min_ctas>;
-    case 1: return (const void*)single_kernel<W, kSingleVariants[1].U, kSingleVariants[1].min_ctas>;
-    case 2: return (const void*)single_kernel<W, kSingleVariants[2].U, kSingleVariants[2].min_ctas>;
-    case 3: return (const void*)single_kernel<W, kSingleVariants[3].U, kSingleVariants[3].min_ctas>;
-    case 4: return (const void*)single_kernel<W, kSingleVariants[4].U, kSingleVariants[4].min_ctas>;
-    case 5: return (const void*)single_kernel<W, kSingleVariants[5].U, kSingleVariants[5].min_ctas>;
-    default: return (const void*)single_kernel<W, kSingleVariants[6].U, kSingleVariants[6].min_ctas>;
+    case 0: return (const void*)single_kernel<W, kSingleVariants[0].U, kSingleVariants[0].G, kSingleVariants[0].min_ctas>;
+    case 1: return (const void*)single_kernel<W, kSingleVariants[1].U, kSingleVariants[1].G, kSingleVariants[1].min_ctas>;
+    case 2: return (const void*)single_kernel<W, kSingleVariants[2].U, kSingleVariants[2].G, kSingleVariants[2].min_ctas>;
+    case 3: return (const void*)single_kernel<W, kSingleVariants[3].U, kSingleVariants[3].G, kSingleVariants[3].min_ctas>;
+    case 4: return (const void*)single_kernel<W, kSingleVariants[4].U, kSingleVariants[4].G, kSingleVariants[4].min_ctas>;
+    case 5: return (const void*)single_kernel<W, kSingleVariants[5].U, kSingleVariants[5].G, kSingleVariants[5].min_ctas>;
+    default: return (const void*)single_kernel<W, kSingleVariants[6].U, kSingleVariants[6].G, kSingleVariants[6].min_ctas>;
     }
 }
 

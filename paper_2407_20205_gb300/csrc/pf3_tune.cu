@@ -85,6 +85,18 @@ int pf3_set_variant(int which, int W, int v)
     return PF3_OK;
 }
 
+int pf3_variant_info(int which, int v, int* U, int* G, int* min_ctas)
+{
+    const KernelVariant* t = nullptr;
+    if (which == 0 && v >= 0 && v < kNumSingleVariants) t = &kSingleVariants[v];
+    if (which == 1 && v >= 0 && v < kNumBatchVariants) t = &kBatchVariants[v];
+    if (!t) return PF3_EINVAL;
+    if (U) *U = t->U;
+    if (G) *G = t->G;
+    if (min_ctas) *min_ctas = t->min_ctas;
+    return PF3_OK;
+}
+
 int pf3_get_variant(int which, int W)
 {
     if (W < 1 || W > 2 || which < 0 || which > 1) return PF3_EINVAL;

@@ -54,3 +54,15 @@ def test_no_oracle_in_product_path():
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src, f
                 assert "perm_f3_oracle" not in src, f
+
+
+def test_binding_check_calls_are_well_formed():
+    """Every _check(rc, what) call in the binding has exactly two arguments."""
+    import ast
+    src = open(os.path.join(ROOT, "paper_2407_20205_gb300", "binding.py")).read()
+    bad = []
+    for node in ast.walk(ast.parse(src)):
+        if isinstance(node, ast.Call) and getattr(node.func, "id", None) == "_check":
+            if len(node.args) != 2:
+                bad.append(node.lineno)
+    assert not bad, bad
