@@ -41,13 +41,15 @@ METRIC = "F3 Ryser Gray-code subsets/sec on 1 GB300; batched perms/sec; p50/p99 
 UNIT = "subsets/s"
 SIZES = (36, 40)
 def i_alg(G: int) -> float:
-    """Minimal ALU-pipe instructions per subset of the grouped walk: per group
-    of 2^G Gray indices, one row step on the low word of the base (3 LOP3),
-    one zero test of the base, and 2^G - 1 probes of two LOP3 each whose zero
-    test is folded into the second gate (LOP3 writes a predicate).  The
-    compiled kernel executes a little more (see profiles/walk_single_n36.md);
-    the fraction against this count is the distance to the best ALU code."""
-    return (3 + 1 + 2 * ((1 << G) - 1)) / (1 << G)
+    """Minimal ALU-pipe instructions per subset of the grouped walk.  Per group
+    of 2^G Gray indices: one row step on the low word of the base (3 LOP3),
+    the base's zero test (1), and 2^G - 1 probes.  A probe needs two LOP3 (the
+    function "column of v + c is nonzero" has four inputs); the second LOP3
+    can also write its zero test as a predicate, and one three-input predicate
+    OR folds two such tests into the group's running flag, so a probe costs at
+    least 2.5 instructions.  The compiled kernel executes a little more (see
+    profiles/walk_single_n36.md)."""
+    return (3 + 1 + 2.5 * ((1 << G) - 1)) / (1 << G)
 
 
 KERNEL_FILES = {"single": ("pf3_device.cuh", "pf3_internal.h", "pf3_single.cu"),
@@ -334,8 +336,8 @@ def run_ours(args):
                 "ops_per_subset": i_alg(g_single),
                 "executed_alu_inst_per_subset": prof.get("alu_inst_per_subset"),
                 "alu_pipe_busy": prof.get("alu_pipe_busy"),
-                "note": f"ops = {i_alg(g_single)} minimal ALU instructions per subset (grouped walk, G = {g_single}; "
-                        f"probes of 2 LOP3 with the zero test folded in); peak = {n_sm} SMs x "
+                "note": f"ops = {i_alg(g_single):.4f} minimal ALU instructions per subset (grouped walk, "
+                        f"G = {g_single}; probes of 2 LOP3 + half a predicate OR); peak = {n_sm} SMs x "
                         f"{sm_max:.0f} MHz x {lanes:.0f} lanes/clk/SM (ALU pipe issue), of measured clock; "
                         f"executed ALU instructions per subset and ALU pipe busy are ncu figures of this kernel"}
         # e2e through the host-pointer C entry point (copies in and out each call)
