@@ -248,17 +248,18 @@ bool launch_once(pf3_ctx* x)
             }
         };
         if (!x->active.empty()) {
-            issue(x->active.front(), budget / 4);
+            // a reserved share for the oldest unfinished request (large
+            // requests always progress), then least remaining work first
+            if (x->cfg.oldest_share > 0) issue(x->active.front(), budget / 100 * (uint64_t)x->cfg.oldest_share);
+            auto remaining = [&](int64_t tk) {
+                const Job& j = x->jobs[tk];
+                return j.nb ? (j.nb - j.cursor) << x->U[j.n <= 32 ? 0 : 1] : (1ull << j.n);
+            };
             std::vector<int64_t> order;
             for (int64_t tk : x->active)
                 if (x->jobs[tk].items_issued < x->jobs[tk].items_total) order.push_back(tk);
-            std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
-                const Job& ja = x->jobs[a];
-                const Job& jb = x->jobs[b];
-                const uint64_t ra = ja.nb ? (ja.nb - ja.cursor) << x->U[ja.n <= 32 ? 0 : 1] : (1ull << ja.n);
-                const uint64_t rb = jb.nb ? (jb.nb - jb.cursor) << x->U[jb.n <= 32 ? 0 : 1] : (1ull << jb.n);
-                return ra < rb;
-            });
+            std::stable_sort(order.begin(), order.end(),
+                             [&](int64_t a, int64_t b) { return remaining(a) < remaining(b); });
             for (int64_t tk : order) {
                 if (budget == 0 || n_items >= x->cfg.launch_items) break;
                 issue(tk, budget);
@@ -370,6 +371,7 @@ void pf3_config_default(pf3_config* cfg)
     cfg->chunk_log2 = 20;
     cfg->launch_items = 16384;
     cfg->max_admit = 1024;
+    cfg->oldest_share = 25;
     cfg->launch_budget = 1ull << 33;
 }
 
@@ -380,7 +382,8 @@ int pf3_create(pf3_ctx** out, const pf3_config* cfg_in)
     pf3_config_default(&cfg);
     if (cfg_in) cfg = *cfg_in;
     if (cfg.max_jobs < 1 || cfg.max_jobs > (1 << 20) || cfg.queue_depth < 1 || cfg.chunk_log2 < 13 ||
-        cfg.chunk_log2 > 62 || cfg.launch_items < 1 || cfg.max_admit < 1 || cfg.launch_budget < 1)
+        cfg.chunk_log2 > 62 || cfg.launch_items < 1 || cfg.max_admit < 1 || cfg.launch_budget < 1 ||
+        cfg.oldest_share < 0 || cfg.oldest_share > 100)
         return PF3_EINVAL;
     int rc;
     DeviceCtx* dc = device_ctx(&rc);
