@@ -256,7 +256,9 @@ int pf3_set_batch_split(int cutoff, int chunk_log2);
 /* Time every variant on the current device and keep the fastest per W.
  * single_ms (pf3_variant_count(0) * 2 doubles) and batch_ms
  * (pf3_variant_count(1) * 2 doubles) receive the timings, W = 1 first; either
- * may be NULL.  Takes about a second. */
+ * may be NULL.  Takes about a second.  When the environment variable
+ * PF3_TUNE_CACHE names a file, the choice is stored there under the GPU's name
+ * and SM count, and later processes load it when they first use the device. */
 int pf3_autotune(double* single_ms, double* batch_ms);
 
 #ifdef __cplusplus

@@ -76,6 +76,7 @@ DeviceCtx* device_ctx(int* rc)
         cudaGetLastError();
         return nullptr;  // leaked partially built context on failure: rare, harmless
     }
+    load_tune_cache(c);
     g_ctx[dev] = c;
     *rc = PF3_OK;
     return c;

@@ -75,6 +75,7 @@ int cuda_rc(cudaError_t e);
 DeviceCtx* device_ctx(int* rc);
 int check_entries_host(const uint8_t* A, int n);
 int single_ctas(DeviceCtx* c, int W, int v);
+void load_tune_cache(DeviceCtx* c);
 int batch_ctas(DeviceCtx* c, int W, int v);
 struct BatchPlan;
 int enqueue_batch(DeviceCtx* c, const BatchPlan& plan, const uint8_t* dAs, uint8_t* d_results,

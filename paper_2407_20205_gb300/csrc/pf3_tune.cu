@@ -8,8 +8,11 @@
 // stream (uniform entries in {0,1,2}).
 #include <cuda_runtime.h>
 
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "perm_f3.h"
@@ -56,6 +59,67 @@ float time_ms(cudaStream_t s, int reps, F fn)
 }
 
 }  // namespace
+
+// Autotune cache: a text file named by the environment variable
+// PF3_TUNE_CACHE, one line per GPU model:
+//   <device name>|<SM count>|<single W=1>|<single W=2>|<batch W=1>|<batch W=2>
+static std::string tune_key(int device)
+{
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return std::string();
+    std::string name(prop.name);
+    for (char& ch : name)
+        if (ch == '|' || ch == '\n') ch = '_';
+    return name + "|" + std::to_string(prop.multiProcessorCount);
+}
+
+void load_tune_cache(DeviceCtx* c)
+{
+    const char* path = std::getenv("PF3_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return;
+    const std::string key = tune_key(c->device);
+    char line[512];
+    while (std::fgets(line, sizeof(line), f)) {
+        std::string l(line);
+        if (l.compare(0, key.size(), key) != 0 || l.size() <= key.size() || l[key.size()] != '|') continue;
+        int v[4];
+        if (std::sscanf(l.c_str() + key.size() + 1, "%d|%d|%d|%d", &v[0], &v[1], &v[2], &v[3]) != 4) continue;
+        if (v[0] < 0 || v[0] >= kNumSingleVariants || v[1] < 0 || v[1] >= kNumSingleVariants || v[2] < 0 ||
+            v[2] >= kNumBatchVariants || v[3] < 0 || v[3] >= kNumBatchVariants)
+            continue;
+        c->single_variant[0] = v[0];
+        c->single_variant[1] = v[1];
+        c->tune.variant[0] = v[2];
+        c->tune.variant[1] = v[3];
+    }
+    std::fclose(f);
+}
+
+static void store_tune_cache(DeviceCtx* c)
+{
+    const char* path = std::getenv("PF3_TUNE_CACHE");
+    if (!path || !*path) return;
+    const std::string key = tune_key(c->device);
+    std::vector<std::string> keep;
+    if (FILE* f = std::fopen(path, "r")) {
+        char line[512];
+        while (std::fgets(line, sizeof(line), f)) {
+            std::string l(line);
+            if (l.compare(0, key.size() + 1, key + "|") != 0) keep.push_back(l);
+        }
+        std::fclose(f);
+    }
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE* f = std::fopen(tmp.c_str(), "w");
+    if (!f) return;
+    for (const auto& l : keep) std::fputs(l.c_str(), f);
+    std::fprintf(f, "%s|%d|%d|%d|%d\n", key.c_str(), c->single_variant[0], c->single_variant[1], c->tune.variant[0],
+                 c->tune.variant[1]);
+    std::fclose(f);
+    std::rename(tmp.c_str(), path);
+}
 
 }  // namespace pf3
 
@@ -196,6 +260,7 @@ int pf3_autotune(double* single_ms, double* batch_ms)
     cudaFree(dout);
     e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) store_tune_cache(c);
     return cuda_rc(e);
 }
 

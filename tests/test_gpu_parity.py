@@ -356,3 +356,28 @@ def test_batch_async_graph_replay(pf3, oracle):
     pf3.perm_f3_batch_async(dAs, ns2, res, hist, s)
     s.synchronize()
     assert res[:count // 2].cpu().numpy().tolist() == want_b[:count // 2].tolist()
+
+
+def test_autotune_cache_roundtrip(tmp_path):
+    """The tuned choice is written to PF3_TUNE_CACHE and loaded by a new process."""
+    import os
+    import subprocess
+    import sys
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    cache = tmp_path / "tune.txt"
+    env = dict(os.environ, PF3_TUNE_CACHE=str(cache))
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_2407_20205_gb300 import binding as b\n"
+            "r = b.autotune()\n"
+            "print(r['single_variant'][1], r['single_variant'][2], r['batch_variant'][1], r['batch_variant'][2])\n") % root
+    first = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
+    line = cache.read_text().strip().splitlines()[-1]
+    assert line.split("|")[-4:] == first.stdout.split()
+    code2 = ("import sys; sys.path.insert(0, %r)\n"
+             "from paper_2407_20205_gb300 import binding as b\n"
+             "print(b.get_variant(0, 1), b.get_variant(0, 2), b.get_variant(1, 1), b.get_variant(1, 2))\n") % root
+    second = subprocess.run([sys.executable, "-c", code2], env=env, capture_output=True, text=True, check=True)
+    assert second.stdout.split() == first.stdout.split()
