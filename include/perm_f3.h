@@ -209,6 +209,25 @@ int pf3_serve_stats(pf3_ctx* ctx, uint64_t* launches, uint64_t* items, uint64_t*
 /* The steady clock the serving times use (ns). */
 uint64_t pf3_now_ns(void);
 
+/* ------------------------------------------------------------ bipedal vectors */
+
+/* Elementwise operations on bipedal vectors (Sec. 2, Theorem 2.1): `count`
+ * vectors of length n <= 64, vector k given by the host words (m1[k], s1[k])
+ * and (m2[k], s2[k]) (column j = bit j); the result (m3[k], s3[k]) is a
+ * bipedal representation of the sum, difference, pointwise product or
+ * pointwise quotient (quotient: meaningful where the divisor is nonzero).
+ * Bits >= n of the results are cleared.  Off the permanent's path. */
+#define PF3_OP_ADD 0
+#define PF3_OP_SUB 1
+#define PF3_OP_MUL 2
+#define PF3_OP_DIV 3
+int pf3_vec_op(int op, int n, int64_t count, const uint64_t* m1, const uint64_t* s1, const uint64_t* m2,
+               const uint64_t* s2, uint64_t* m3, uint64_t* s3);
+
+/* psi of Sec. 2: vectors (mag[k], sgn[k]) back to entries {0,1,2} (2 == -1),
+ * out: host, count * n bytes, vector k's entries at out[k*n .. k*n + n). */
+int pf3_vec_unpack(int n, int64_t count, const uint64_t* mag, const uint64_t* sgn, uint8_t* out);
+
 /* ------------------------------------------------------------ diagnostics */
 
 /* The row step on every case: for state s in 0..3 ((mag, sgn) = (s>>1, s&1)),

@@ -345,6 +345,39 @@ class ServeContext:
         return {"launches": a.value, "items": b.value, "jobs_done": c.value}
 
 
+# ------------------------------------------------------------ bipedal vectors
+
+OP_ADD, OP_SUB, OP_MUL, OP_DIV = 0, 1, 2, 3
+_lib_vecop = _sig("pf3_vec_op", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int64, _u64p, _u64p, _u64p,
+                                               _u64p, _u64p, _u64p])
+_lib_unpack = _sig("pf3_vec_unpack", ctypes.c_int, [ctypes.c_int, ctypes.c_int64, _u64p, _u64p, _u8p])
+
+
+def _u64(a):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.uint64))
+    return a, a.ctypes.data_as(_u64p)
+
+
+def vec_op(op: int, n: int, m1, s1, m2, s2):
+    """Elementwise bipedal add/sub/mul/div of arrays of vectors (Theorem 2.1)."""
+    (m1, p1), (s1, q1), (m2, p2), (s2, q2) = _u64(m1), _u64(s1), _u64(m2), _u64(s2)
+    count = int(m1.shape[0])
+    m3 = np.zeros(count, np.uint64)
+    s3 = np.zeros(count, np.uint64)
+    _check(_lib_vecop(op, n, count, p1, q1, p2, q2, m3.ctypes.data_as(_u64p), s3.ctypes.data_as(_u64p)),
+           "pf3_vec_op")
+    return m3, s3
+
+
+def vec_unpack(n: int, mag, sgn) -> np.ndarray:
+    """psi: uint8[count, n] entries in {0,1,2}."""
+    (m, p), (s, q) = _u64(mag), _u64(sgn)
+    count = int(m.shape[0])
+    out = np.zeros((count, n), np.uint8)
+    _check(_lib_unpack(n, count, p, q, out.ctypes.data_as(_u8p)), "pf3_vec_unpack")
+    return out
+
+
 # ------------------------------------------------------------ diagnostics
 
 def step_table() -> np.ndarray:
@@ -427,5 +460,6 @@ def exported_symbols() -> list[str]:
                         "pf3_config_default", "pf3_create", "pf3_destroy", "perm_f3_submit", "perm_f3_poll",
                         "perm_f3_wait", "pf3_job_times", "pf3_serve_stats", "pf3_now_ns",
                         "pf3_cancel_queued", "pf3_longrun", "pf3_longrun_cancel",
-                        "pf3_count_exhaustive", "pf3_variant_info")
+                        "pf3_count_exhaustive", "pf3_variant_info", "pf3_vec_op",
+                        "pf3_vec_unpack")
             if hasattr(_lib, n)]
