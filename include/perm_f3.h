@@ -244,7 +244,8 @@ int pf3_pack(const uint8_t* A, int n, uint64_t* mag, uint64_t* sgn);
  * 0 LOP3, 1 IMAD, 2 IADD, 3 LOP3+IMAD, 4 full row step (3 LOP3 + compare),
  * 5 POPC, 6 MAX(+IMAD), 7 2 LOP3 + MAX, 8 probe (2 LOP3 + compare),
  * 9 row step + IMAD, 10 2 LOP3 + IADD, 11 probe with inverted gate tested
- * against zero, 12 probe tested against all ones (2 LOP3 + compare each).
+ * against zero, 12 probe tested against all ones, 13 inverted probe with an AND
+ * chain of "nonzero" (2 LOP3 + compare each).
  * Runs `ctas_per_sm` CTAs of `threads` threads per SM for `iters` rounds and
  * reports instructions per clock per SM (thread instructions, i.e. lanes),
  * thread instructions per second over the whole GPU, and the SM clock in MHz

@@ -397,7 +397,7 @@ def pack(A) -> tuple[np.ndarray, np.ndarray]:
 
 INTPIPE_KINDS = {"lop3": 0, "imad": 1, "iadd": 2, "lop3_imad": 3, "step": 4, "popc": 5, "max_imad": 6,
                  "lop3x2_max": 7, "probe": 8, "step_imad": 9, "lop3x2_iadd": 10, "probe_inv": 11,
-                 "probe_ones": 12}
+                 "probe_ones": 12, "probe_and": 13}
 
 
 def intpipe_bench(kind, ctas_per_sm: int = 4, threads: int = 256, iters: int = 4096) -> dict:

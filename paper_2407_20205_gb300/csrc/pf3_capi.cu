@@ -252,8 +252,8 @@ int pf3_pack(const uint8_t* A, int n, uint64_t* mag, uint64_t* sgn)
 int pf3_intpipe_bench(int kind, int ctas_per_sm, int threads, int iters, double* inst_per_clk_per_sm,
                       double* inst_per_s, double* sm_mhz)
 {
-    static const int per_op[13] = {1, 1, 1, 2, 4, 3, 2, 3, 3, 4, 3, 3, 3};
-    if (kind < 0 || kind > 12 || ctas_per_sm < 1 || threads < 32 || threads > 1024 || (threads & 31) || iters < 1)
+    static const int per_op[14] = {1, 1, 1, 2, 4, 3, 2, 3, 3, 4, 3, 3, 3, 3};
+    if (kind < 0 || kind > 13 || ctas_per_sm < 1 || threads < 32 || threads > 1024 || (threads & 31) || iters < 1)
         return PF3_EINVAL;
     int rc;
     DeviceCtx* c = device_ctx(&rc);

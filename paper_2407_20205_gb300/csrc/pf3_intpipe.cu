@@ -12,7 +12,8 @@
 // one max, 8 = two LOP3 and an accumulating compare (the probe of the walk),
 // 9 = three LOP3 and one IMAD, 10 = two LOP3 and one integer add, 11 = the
 // probe with an inverted last gate tested against zero, 12 = the probe tested
-// against all ones (both: two LOP3 and one compare per op).
+// against all ones, 13 = the inverted probe accumulated with AND of "nonzero"
+// (each: two LOP3 and one compare per op).
 #include <cuda_runtime.h>
 
 #include "pf3_device.cuh"
@@ -38,6 +39,7 @@ __global__ void intpipe_kernel(uint32_t* sink, unsigned long long* cycles, int i
     const uint32_t ka = one * 0x0F0F0F0Fu, kb = one * 0x33333333u, kc = one * 0x55555555u,
                    kd = one * 0x00FF00FFu;
     bool hit = false;
+    bool allnz = true;
     __syncthreads();
     const unsigned long long t0 = clock64();
     for (int it = 0; it < iters; ++it) {
@@ -87,6 +89,13 @@ __global__ void intpipe_kernel(uint32_t* sink, unsigned long long* cycles, int i
                     hit |= (nm == 0u);
                     x[c] = gq;
                     y[c] = nm;
+                } else if (KIND == 13) {
+                    // inverted gate, accumulated as "every probe has a zero column"
+                    const uint32_t gq = lop3<kLutG>(y[c], (u & 1) ? ka : kc, (u & 1) ? kb : kd);
+                    const uint32_t nm = lop3<(~kLutMag) & 0xFF>(x[c], (u & 1) ? ka : kc, gq);
+                    allnz &= (nm != 0u);
+                    x[c] = gq;
+                    y[c] = nm;
                 } else if (KIND == 12) {
                     // the walk's probe as written (test against all ones), same chain
                     const uint32_t gq = lop3<kLutG>(y[c], (u & 1) ? ka : kc, (u & 1) ? kb : kd);
@@ -99,7 +108,7 @@ __global__ void intpipe_kernel(uint32_t* sink, unsigned long long* cycles, int i
         }
     }
     const unsigned long long t1 = clock64();
-    uint32_t acc = hit ? 1u : 0u;
+    uint32_t acc = (hit ? 1u : 0u) ^ (allnz ? 2u : 0u);
 #pragma unroll
     for (int c = 0; c < kChains; ++c) acc ^= x[c] ^ y[c] ^ z[c];
     sink[blockIdx.x * blockDim.x + threadIdx.x] = acc;
@@ -125,6 +134,7 @@ cudaError_t launch_intpipe(int kind, int grid, int threads, int iters, uint32_t*
     case 10: intpipe_kernel<10><<<grid, threads, 0, stream>>>(sink, cycles, iters, 1u); break;
     case 11: intpipe_kernel<11><<<grid, threads, 0, stream>>>(sink, cycles, iters, 1u); break;
     case 12: intpipe_kernel<12><<<grid, threads, 0, stream>>>(sink, cycles, iters, 1u); break;
+    case 13: intpipe_kernel<13><<<grid, threads, 0, stream>>>(sink, cycles, iters, 1u); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
