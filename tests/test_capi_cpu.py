@@ -66,3 +66,21 @@ def test_binding_check_calls_are_well_formed():
             if len(node.args) != 2:
                 bad.append(node.lineno)
     assert not bad, bad
+
+
+def test_header_is_c99_and_links(tmp_path, libpath):
+    """A C99 program that references every declared function compiles against
+    include/perm_f3.h and links with the library (it is not run: no GPU)."""
+    names = declared_functions()
+    body = "\n".join(f"    p[{k}] = (void (*)(void))&{n};" for k, n in enumerate(names))
+    src = tmp_path / "uses_all.c"
+    src.write_text(
+        '#include "perm_f3.h"\n#include <stdio.h>\n'
+        f"int main(void) {{\n    void (*p[{len(names)}])(void);\n{body}\n"
+        '    printf("%p\\n", (void*)p[0]);\n    return 0;\n}\n')
+    exe = tmp_path / "uses_all"
+    libdir = os.path.dirname(libpath)
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe), "-L", libdir, "-lperm_f3", f"-Wl,-rpath,{libdir}"], check=True, capture_output=True,
+                   text=True)
+    assert exe.exists()
