@@ -228,7 +228,7 @@ def run_reference(args):
     value = per_step * args.steps / dt
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
-            "scaling": "strong", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "scaling": "strong", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": workload_config(),
             "impl": "reference",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": th, "kind": "oracle",
@@ -369,7 +369,7 @@ def run_ours(args):
             cpu = cpu_sample(mats[36])
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-                "scaling": "strong", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+                "scaling": "strong", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
                 "config": {**workload_config(),
                            "results": {str(n): results[n] for n in SIZES},
                            "ms_per_launch": {str(n): float(np.mean(v)) for n, v in launch_ms.items()},
