@@ -2,14 +2,15 @@
 // plane width (the Monte Carlo workload of Sec. 4: permanents of many random
 // matrices).
 //
-// The host plans work items: a matrix with n <= cutoff is one item walked by
-// one warp (its 32 lanes split the 2^(n-U) Gray blocks); a larger matrix is
-// cut into items of 2^chunk_log2 Gray indices (Sec. 3.1's blocks of
-// consecutive Gray states), whose counts meet in per-matrix accumulators; the
-// warp that finishes a matrix's last item maps its counts to perm mod 3.
-// Items are sorted largest first and handed out through an atomic cursor, so
-// the grid stays full until the end.  Each warp packs its matrix into its own
-// shared-memory row table.
+// The host plans work items: up to 32 consecutive matrices of the same small
+// n (n <= 10) form one item walked one matrix per lane; a matrix with
+// 10 < n <= cutoff is one item walked by one warp (its 32 lanes split the
+// 2^(n-U) Gray blocks); a larger matrix is cut into items of 2^chunk_log2
+// Gray indices (Sec. 3.1's blocks of consecutive Gray states), whose counts
+// meet in per-matrix accumulators; the warp that finishes a matrix's last
+// item maps its counts to perm mod 3.  Items are sorted largest first and
+// handed out through an atomic cursor, so the grid stays full until the end.
+// Each warp packs its matrix into its own shared-memory row table.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -131,7 +132,7 @@ __global__ void __launch_bounds__(kBatchThreads, MINB) batch_kernel(BatchArgs a)
         Counts c{0ull, 0ull};
         if (!bad && n > 0) {
             if (it.NB == 0) {
-                // small n: one lane walks all 2^n indices
+                // n <= U (serving items): one lane walks all 2^n indices
                 if (lane == 0) walk_generic<W>(tab, n, 0, (n == 64) ? ~0ull : ((1ull << n) - 1), c);
             } else {
                 GroupRows<G, U> R;
