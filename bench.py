@@ -195,9 +195,14 @@ def cpu_sample(A, seconds_target=12.0, max_log2=34):
                     t0 = time.perf_counter()
                     oracle.ryser_range_par(At, 0, cnt - 1, nparts=threads * 4, nthreads=threads)
                     dt = time.perf_counter() - t0
+            # one core, for comparison with single-core figures
+            t1 = time.perf_counter()
+            oracle.ryser_range(At, 0, (1 << 22) - 1)
+            single = (1 << 22) / (time.perf_counter() - t1)
             return {"value": cnt / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
                     "sample": f"Gray indices 0..2^{lg}-1 of the seeded {A.shape[0]}x{A.shape[0]} matrix "
-                              f"({cnt} subsets, {dt:.2f} s wall on {threads} threads)"}
+                              f"({cnt} subsets, {dt:.2f} s wall on {threads} threads)",
+                    "single_core_value": single}
         lg += 2
 
 

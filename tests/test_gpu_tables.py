@@ -48,3 +48,29 @@ def test_table3_monte_carlo_gpu(pf3, n, trials):
     sd = math.sqrt(p * (1 - p) / trials)
     assert abs(z / trials - p) < 4.5 * sd
     assert abs(o - t) < 5 * math.sqrt(trials)
+
+
+def test_config3_full_batch_sampled_and_histogram(pf3, oracle):
+    """The 200,000-matrix 24 x 24 workload in the launch the benchmark times:
+    sampled results against the oracle one by one, and the histogram
+    statistics of Sec. 4 (P(0) near 1/3 at n = 24, #1 and #2 equal in law)."""
+    import numpy as np
+    import torch
+    from paper_2407_20205_gb300 import inputs
+    count, n = 200000, 24
+    A = inputs.uniform_matrices(inputs.SEED_BATCH24, n, count)
+    dAs = torch.from_numpy(A.reshape(-1)).cuda()
+    res = torch.zeros(count, dtype=torch.uint8, device="cuda")
+    hist = torch.zeros(3, dtype=torch.int64, device="cuda")
+    s = torch.cuda.Stream()
+    pf3.perm_f3_batch_async(dAs, np.full(count, n, np.int32), res, hist, s)
+    s.synchronize()
+    r = res.cpu().numpy()
+    h = hist.cpu().numpy().tolist()
+    assert h == [int((r == v).sum()) for v in range(3)] and sum(h) == count
+    idx = sorted(set(list(range(48)) + list(range(48, count, count // 160))))
+    want = oracle.perm_batch([A[k] for k in idx])
+    assert r[idx].tolist() == want.tolist()
+    sd = math.sqrt(count * (1 / 3) * (2 / 3))
+    assert abs(h[0] - count / 3) < 4 * sd
+    assert abs(h[1] - h[2]) < 4 * math.sqrt(2 * count / 3)
