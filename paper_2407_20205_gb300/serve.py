@@ -126,12 +126,15 @@ def main():
     ap.add_argument("--no-fifo", action="store_true")
     ap.add_argument("--oldest-share", type=int, default=None, help="percent of each launch for the oldest request")
     ap.add_argument("--chunk-log2", type=int, default=None)
+    ap.add_argument("--launch-budget-log2", type=int, default=None)
     a = ap.parse_args()
     cfg = {}
     if a.oldest_share is not None:
         cfg["oldest_share"] = a.oldest_share
     if a.chunk_log2 is not None:
         cfg["chunk_log2"] = a.chunk_log2
+    if a.launch_budget_log2 is not None:
+        cfg["launch_budget"] = 1 << a.launch_budget_log2
     out, _, _ = run(a.jobs, a.nmin, a.nmax, a.rho, capacity=a.capacity, fifo=not a.no_fifo, cfg_overrides=cfg)
     print(json.dumps(out))
 
