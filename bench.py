@@ -276,7 +276,7 @@ def run_ours(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    tune = pf3.autotune()  # picks the kernel variants (untimed)
+    tune = pf3.autotune()  # picks the kernel variants and batch planning (untimed)
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             step()
@@ -380,7 +380,11 @@ def run_ours(args):
                            "ms_per_launch": {str(n): float(np.mean(v)) for n, v in launch_ms.items()},
                            "parallelism": f"range split x{world}" if world > 1 else "1 GPU",
                            "variants": {"single": tune["single_variant"], "batch": tune["batch_variant"]},
-                           "autotune_ms": {"single": tune["single_ms"], "batch": tune["batch_ms"]}},
+                           "batch_tuning": tune["batch_tuning"],
+                           "autotune_ms": {"single": tune["single_ms"], "batch": tune["batch_ms"],
+                                           "pack_packed_vs_warp": {str(n): v for n, v in tune["pack_ms"].items()},
+                                           "split_items_per_warp": {str(g): v for g, v in
+                                                                    tune["split_ms"].items()}}},
                 "clocks": clk, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": len(SIZES) * args.steps, "wall_s_timed": t_wall, "extra": extra}
         print(json.dumps(line), flush=True)

@@ -52,7 +52,7 @@ extern "C" {
 #define PF3_ETIMEDOUT (-5)   /* perm_f3_wait: the deadline passed */
 #define PF3_ECANCELED (-6)   /* the job or context was cancelled */
 #define PF3_EBUSY (-7)       /* perm_f3_submit: the request queue is full */
-#define PF3_ETOOBIG (-8)     /* more CTAs requested than the fixed no-allocation scratch holds */
+#define PF3_ETOOBIG (-8)     /* request larger than a fixed buffer: no-allocation scratch, output array */
 
 #define PF3_MAX_N 64
 
@@ -269,17 +269,90 @@ int pf3_get_variant(int which, int W);
  * indices per carried base state, minimum resident CTAs per SM. */
 int pf3_variant_info(int which, int v, int* U, int* G, int* min_ctas);
 
+/* Threads per CTA of variant v (which as above), or PF3_EINVAL. */
+int pf3_variant_threads(int which, int v);
+
 /* Batch work split: matrices with n > cutoff are cut into work items of
- * 2^chunk_log2 Gray indices (Sec. 3.1 blocks); others are one item each. */
+ * 2^chunk_log2 Gray indices (Sec. 3.1 blocks); others are one item each.
+ * chunk_log2 in 12..62, or 0 for the automatic split (see
+ * pf3_set_batch_tuning; cutoff is then unused).  PF3_EINVAL otherwise. */
 int pf3_set_batch_split(int cutoff, int chunk_log2);
 
-/* Time every variant on the current device and keep the fastest per W.
+/* All batch planning parameters (the autotuner sets tiny_cutoff and
+ * items_per_warp and selects the automatic split):
+ *   tiny_cutoff     0..PF3_TINY_MAX_N: matrices with n <= tiny_cutoff are
+ *                   packed 32 to a warp and walked one per lane (the packing
+ *                   cutoff); larger ones get at least a whole warp;
+ *   split_cutoff    0..64, chunk_log2 12..62: fixed split, as
+ *                   pf3_set_batch_split;
+ *   chunk_log2 = 0  guided split: per plane width, the non-packed matrices
+ *                   are taken largest first (2^n Gray indices each) and each
+ *                   is cut into items (Sec. 3.1 blocks) no longer than the
+ *                   work from that matrix to the end of the order divided by
+ *                   (warps of the persistent grid x items_per_warp), rounded
+ *                   down to a power of two and at least 2^20 indices, so the
+ *                   last items handed out are short and the warps finish
+ *                   together;
+ *   items_per_warp  1..1024, the divisor of the guided split.
+ * Results never depend on these, only speed does.  PF3_EINVAL on a value out
+ * of range. */
+#define PF3_TINY_MAX_N 16
+int pf3_set_batch_tuning(int tiny_cutoff, int split_cutoff, int chunk_log2, int items_per_warp);
+int pf3_get_batch_tuning(int* tiny_cutoff, int* split_cutoff, int* chunk_log2, int* items_per_warp);
+
+/* One work item of a batch plan (diagnostic view).  kind: 0 = a whole matrix
+ * walked by one warp, 1 = one piece of a split matrix, 2 = a packed group of
+ * num_blocks consecutive matrices (index mat, mat + 1, ...) of the same n
+ * walked one per lane, 3 = a matrix with n <= block_log2 walked by one lane.
+ * Kinds 0 and 1 cover Gray indices [first_block, first_block + num_blocks) x
+ * 2^block_log2 of matrix mat; cls is 0 for n <= 32 (one word per plane), 1
+ * otherwise. */
+typedef struct {
+    int64_t mat;
+    int32_t n;
+    int32_t kind;
+    uint64_t first_block;
+    uint64_t num_blocks;
+    int32_t block_log2;
+    int32_t cls;
+} pf3_plan_item;
+
+/* The batch planner on the host alone (no device is touched): the work items
+ * perm_f3_batch would launch for sizes ns[count] under the given tuning
+ * (tiny_cutoff, split_cutoff, chunk_log2, items_per_warp as
+ * pf3_set_batch_tuning), batch kernel variants variant[2] and persistent grids
+ * of warps[2] warps, in launch order per class (class 1 first, each sorted
+ * largest first).  items (host, capacity entries) may be NULL to ask for the
+ * count only; *num_items receives the number of items; auto_chunk_log2[2]
+ * (may be NULL) receives, per class, log2 of the longest item of its largest
+ * matrix (0 for a class without such matrices).  PF3_EINVAL on a bad argument, PF3_ETOOBIG when
+ * capacity < *num_items (nothing written to items). */
+int pf3_batch_plan(const int32_t* ns, int64_t count, int tiny_cutoff, int split_cutoff, int chunk_log2,
+                   int items_per_warp, const int* variant, const int* warps, pf3_plan_item* items, int64_t capacity,
+                   int64_t* num_items, int* auto_chunk_log2);
+
+/* Time every variant on the current device and keep the fastest per W, then
+ * pick the batch packing cutoff and split granularity (pf3_autotune_ex).
  * single_ms (pf3_variant_count(0) * 2 doubles) and batch_ms
- * (pf3_variant_count(1) * 2 doubles) receive the timings, W = 1 first; either
- * may be NULL.  Takes about a second.  When the environment variable
- * PF3_TUNE_CACHE names a file, the choice is stored there under the GPU's name
- * and SM count, and later processes load it when they first use the device. */
+ * (pf3_variant_count(1) * 2 doubles) receive the variant timings, W = 1
+ * first; either may be NULL.  Takes a few seconds.  When the environment
+ * variable PF3_TUNE_CACHE names a file, the choice is stored there under the
+ * GPU's name and SM count, and later processes load it when they first use
+ * the device. */
 int pf3_autotune(double* single_ms, double* batch_ms);
+
+/* pf3_autotune with the timings of its batch planning stages:
+ * pack_ms (2 * (PF3_TINY_MAX_N + 1) doubles, may be NULL): [n] the packed
+ * walk and [PF3_TINY_MAX_N + 1 + n] the warp walk of a full grid of n x n
+ * matrices, for n from the W = 1 batch variant's U + 1 up to the first n at
+ * which the warp walk is as fast (0 where not timed); the packing cutoff is
+ * the last n at which the packed walk was faster (at least min(U, 16)).
+ * split_ms (PF3_SPLIT_CANDIDATES doubles, may be NULL): three batches
+ * (3000 x n = 26; 300 x 28 + 600 x 26 + 1200 x 24; 20 x 33 + 6 x 34) under
+ * the guided split with items_per_warp 1, 2, 4, 8, 16; the fastest total is
+ * kept, ties within 1 % going to fewer items.  Takes a few seconds. */
+#define PF3_SPLIT_CANDIDATES 5
+int pf3_autotune_ex(double* single_ms, double* batch_ms, double* pack_ms, double* split_ms);
 
 #ifdef __cplusplus
 }

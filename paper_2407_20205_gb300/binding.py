@@ -77,7 +77,23 @@ _lib_setv = _sig("pf3_set_variant", ctypes.c_int, [ctypes.c_int, ctypes.c_int, c
 _lib_getv = _sig("pf3_get_variant", ctypes.c_int, [ctypes.c_int, ctypes.c_int])
 _lib_vinfo = _sig("pf3_variant_info", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _ip, _ip, _ip])
 _lib_split = _sig("pf3_set_batch_split", ctypes.c_int, [ctypes.c_int, ctypes.c_int])
+_lib_vthreads = _sig("pf3_variant_threads", ctypes.c_int, [ctypes.c_int, ctypes.c_int])
 _lib_autotune = _sig("pf3_autotune", ctypes.c_int, [_dp, _dp])
+_lib_autotune_ex = _sig("pf3_autotune_ex", ctypes.c_int, [_dp, _dp, _dp, _dp])
+_lib_set_btune = _sig("pf3_set_batch_tuning", ctypes.c_int, [ctypes.c_int] * 4)
+_lib_get_btune = _sig("pf3_get_batch_tuning", ctypes.c_int, [_ip] * 4)
+
+
+class PlanItem(ctypes.Structure):
+    _fields_ = [("mat", ctypes.c_int64), ("n", ctypes.c_int32), ("kind", ctypes.c_int32),
+                ("first_block", ctypes.c_uint64), ("num_blocks", ctypes.c_uint64), ("block_log2", ctypes.c_int32),
+                ("cls", ctypes.c_int32)]
+
+
+_lib_plan = _sig("pf3_batch_plan", ctypes.c_int,
+                 [ctypes.POINTER(ctypes.c_int32), ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                  ctypes.c_int, _ip, _ip, ctypes.POINTER(PlanItem), ctypes.c_int64,
+                  ctypes.POINTER(ctypes.c_int64), _ip])
 
 
 class PF3Error(RuntimeError):
@@ -434,21 +450,67 @@ def get_variant(which: int, W: int) -> int:
 def variant_info(which: int, v: int) -> dict:
     U, G, mc = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(_lib_vinfo(which, v, ctypes.byref(U), ctypes.byref(G), ctypes.byref(mc)), "pf3_variant_info")
-    return {"U": U.value, "G": G.value, "min_ctas": mc.value}
+    return {"U": U.value, "G": G.value, "min_ctas": mc.value,
+            "threads": _check(_lib_vthreads(which, v), "pf3_variant_threads")}
 
 
 def set_batch_split(cutoff: int, chunk_log2: int) -> None:
     _check(_lib_split(cutoff, chunk_log2), "pf3_set_batch_split")
 
 
+TINY_MAX_N = 16
+SPLIT_CANDIDATES = (1, 2, 4, 8, 16)
+
+
+def set_batch_tuning(tiny_cutoff: int, split_cutoff: int, chunk_log2: int, items_per_warp: int) -> None:
+    _check(_lib_set_btune(tiny_cutoff, split_cutoff, chunk_log2, items_per_warp), "pf3_set_batch_tuning")
+
+
+def get_batch_tuning() -> dict:
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(_lib_get_btune(*[ctypes.byref(x) for x in v]), "pf3_get_batch_tuning")
+    return dict(zip(("tiny_cutoff", "split_cutoff", "chunk_log2", "items_per_warp"), (x.value for x in v)))
+
+
+PLAN_KINDS = ("whole", "piece", "packed", "lane")
+
+
+def batch_plan(ns, tiny_cutoff: int = 10, split_cutoff: int = 28, chunk_log2: int = 0, items_per_warp: int = 8,
+               variant=(0, 0), warps=(2432, 2432)) -> dict:
+    """The batch planner's work items for sizes `ns`, computed on the host
+    (no device needed): launch order per class, as perm_f3_batch would run
+    them."""
+    nsa = np.ascontiguousarray(np.asarray(ns, dtype=np.int32))
+    p = nsa.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    va = (ctypes.c_int * 2)(*variant)
+    wa = (ctypes.c_int * 2)(*warps)
+    num = ctypes.c_int64()
+    cl = (ctypes.c_int * 2)()
+    args = (p, len(nsa), tiny_cutoff, split_cutoff, chunk_log2, items_per_warp, va, wa)
+    _check(_lib_plan(*args, None, 0, ctypes.byref(num), cl), "pf3_batch_plan")
+    buf = (PlanItem * max(1, num.value))()
+    _check(_lib_plan(*args, buf, num.value, ctypes.byref(num), cl), "pf3_batch_plan")
+    items = [{"mat": x.mat, "n": x.n, "kind": PLAN_KINDS[x.kind], "first_block": x.first_block,
+              "num_blocks": x.num_blocks, "block_log2": x.block_log2, "cls": x.cls} for x in buf[:num.value]]
+    return {"items": items, "chunk_log2": [cl[0], cl[1]]}
+
+
 def autotune() -> dict:
+    """Variant timings per W, the packed and warp walk times per n (packing
+    cutoff), the split-granularity timings, and the choices made."""
     ns, nb = variant_count(SINGLE), variant_count(BATCH)
     a = (ctypes.c_double * (2 * ns))()
     b = (ctypes.c_double * (2 * nb))()
-    _check(_lib_autotune(a, b), "pf3_autotune")
+    pk = (ctypes.c_double * (2 * (TINY_MAX_N + 1)))()
+    sp = (ctypes.c_double * len(SPLIT_CANDIDATES))()
+    _check(_lib_autotune_ex(a, b, pk, sp), "pf3_autotune_ex")
+    pk = list(pk)
     return {"single_ms": {1: list(a)[:ns], 2: list(a)[ns:]}, "batch_ms": {1: list(b)[:nb], 2: list(b)[nb:]},
+            "pack_ms": {n: [pk[n], pk[TINY_MAX_N + 1 + n]] for n in range(TINY_MAX_N + 1) if pk[n] > 0},
+            "split_ms": dict(zip(SPLIT_CANDIDATES, list(sp))),
             "single_variant": {W: get_variant(SINGLE, W) for W in (1, 2)},
-            "batch_variant": {W: get_variant(BATCH, W) for W in (1, 2)}}
+            "batch_variant": {W: get_variant(BATCH, W) for W in (1, 2)},
+            "batch_tuning": get_batch_tuning()}
 
 
 def exported_symbols() -> list[str]:
@@ -461,5 +523,6 @@ def exported_symbols() -> list[str]:
                         "perm_f3_wait", "pf3_job_times", "pf3_serve_stats", "pf3_now_ns",
                         "pf3_cancel_queued", "pf3_longrun", "pf3_longrun_cancel",
                         "pf3_count_exhaustive", "pf3_variant_info", "pf3_vec_op",
-                        "pf3_vec_unpack")
+                        "pf3_vec_unpack", "pf3_set_batch_tuning", "pf3_get_batch_tuning",
+                        "pf3_autotune_ex", "pf3_batch_plan", "pf3_variant_threads")
             if hasattr(_lib, n)]

@@ -3,17 +3,20 @@
 // matrices).
 //
 // The host plans work items: up to 32 consecutive matrices of the same small
-// n (n <= 10) form one item walked one matrix per lane; a matrix with
-// 10 < n <= cutoff is one item walked by one warp (its 32 lanes split the
-// 2^(n-U) Gray blocks); a larger matrix is cut into items of 2^chunk_log2
-// Gray indices (Sec. 3.1's blocks of consecutive Gray states), whose counts
-// meet in per-matrix accumulators; the warp that finishes a matrix's last
-// item maps its counts to perm mod 3.  Items are sorted largest first and
-// handed out through an atomic cursor, so the grid stays full until the end.
-// Each warp packs its matrix into its own shared-memory row table.
+// n (n <= the packing cutoff, at most 16) form one item walked one matrix per
+// lane; a larger matrix is one item walked by one warp (its 32 lanes split
+// the 2^(n-U) Gray blocks) unless it is cut into items of consecutive Gray
+// indices (Sec. 3.1's blocks of consecutive Gray states), whose counts meet
+// in per-matrix accumulators; the warp that finishes a matrix's last item
+// maps its counts to perm mod 3.  The item length is fixed or sized from the
+// batch's total work so that every warp of the grid gets several items.
+// Items are sorted largest first and handed out through an atomic cursor, so
+// the grid stays full until the end.  Each warp packs its matrix into its own
+// shared-memory row table.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <numeric>
@@ -34,10 +37,10 @@ constexpr unsigned kBadBit = 0x80000000u;
 // Per-lane row masks of one tiny matrix: [row][component][lane], component
 // 0 = K1, 1 = K2 (add), 2 = K2 (subtract).
 struct TinyTable {
-    uint32_t k[kTinyN][3][32];
+    uint32_t k[kTinyMaxN][3][32];
 };
 
-// One lane: pack its n x n matrix (n <= kTinyN) and walk all 2^n Gray
+// One lane: pack its n x n matrix (n <= kTinyMaxN) and walk all 2^n Gray
 // indices with the row step of Sec. 2 (Theorem 2.1 semantics), full zero test
 // and popcount sign at every index.  Returns perm mod 3, or 255 on a bad entry.
 __device__ __forceinline__ int tiny_perm(TinyTable& T, const uint8_t* A, int n, int lane)
@@ -230,80 +233,123 @@ cudaError_t launch_slot_init(const SlotInit* inits, int count, const uint8_t* st
 
 // ---------------------------------------------------------------- planning
 
-void plan_batch(const int32_t* ns, int64_t count, const BatchTuning& tune, BatchPlan& plan)
+// Largest power-of-two exponent e with 2^e <= x (x >= 1), capped at 63.
+static int floor_log2(double x)
+{
+    int e = 0;
+    while (e < 63 && std::ldexp(1.0, e + 1) <= x) ++e;
+    return e;
+}
+
+static WorkItem make_item(long long offset, int64_t mat, int n)
+{
+    WorkItem it;
+    std::memset(&it, 0, sizeof(it));
+    it.offset = offset;
+    it.mat = (int)mat;
+    it.n = n;
+    it.split = -1;
+    return it;
+}
+
+void plan_batch(const int32_t* ns, int64_t count, const BatchTuning& tune, const int warps[2], BatchPlan& plan)
 {
     const int Ucls[2] = {kBatchVariants[tune.variant[0]].U, kBatchVariants[tune.variant[1]].U};
+    const int tiny = std::min(tune.tiny_cutoff, kTinyMaxN);
     plan.items[0].clear();
     plan.items[1].clear();
     plan.split_items.clear();
     plan.num_split = 0;
     plan.total_bytes = 0;
+    plan.chunk_log2[0] = plan.chunk_log2[1] = 0;
+    std::vector<long long> offset((size_t)count);
     long long off = 0;
     for (int64_t k = 0; k < count; ++k) {
-        const int n = ns[k];
-        if (n <= kTinyN) {
-            // a run of up to 32 consecutive matrices with this same small n
-            int64_t e = k + 1;
-            while (e < count && e - k < 32 && ns[e] == n) ++e;
-            WorkItem it;
-            std::memset(&it, 0, sizeof(it));
-            it.offset = off;
-            it.mat = (int)k;
-            it.n = n;
-            it.split = kTinyItem;
-            it.B0 = 0;
-            it.NB = (unsigned long long)(e - k);
-            plan.items[0].push_back(it);
-            off += (long long)n * n * (e - k);
-            k = e - 1;
-            continue;
-        }
-        WorkItem it;
-        std::memset(&it, 0, sizeof(it));
-        it.offset = off;
-        it.mat = (int)k;
-        it.n = n;
-        it.split = -1;
-        const int cls = n <= 32 ? 0 : 1;
-        const int U = Ucls[cls];
-        off += (long long)n * n;
-        if (n < U + 1) {
-            it.B0 = 0;
-            it.NB = 0;  // generic walk by one lane
-            plan.items[cls].push_back(it);
-            continue;
-        }
-        const uint64_t NB = (n == 64) ? (1ull << (64 - U)) : (1ull << (n - U));
-        if (n <= tune.cutoff) {
-            it.B0 = 0;
-            it.NB = NB;
-            plan.items[cls].push_back(it);
-            continue;
-        }
-        // at most 2^20 items per matrix keeps the item table small for n near 64
-        const int cl = std::max(std::max(tune.chunk_log2, U + 5), n - 20);
-        const uint64_t per = 1ull << (cl - U);
-        const uint64_t nitems = (NB + per - 1) / per;
-        it.split = plan.num_split++;
-        plan.split_items.push_back((unsigned)nitems);
-        for (uint64_t q = 0; q < nitems; ++q) {
-            it.B0 = q * per;
-            it.NB = std::min<unsigned long long>(per, NB - it.B0);
-            plan.items[cls].push_back(it);
-        }
+        offset[(size_t)k] = off;
+        off += (long long)ns[k] * ns[k];
     }
     plan.total_bytes = off;
-    // largest first (longest-processing-time order); ties keep matrix order.
-    // Cost = Gray indices one warp walks (a tiny item's lanes run in parallel).
+
+    // packed groups: runs of up to 32 consecutive matrices with one small n
+    for (int64_t k = 0; k < count; ++k) {
+        const int n = ns[k];
+        if (n > tiny) continue;
+        int64_t e = k + 1;
+        while (e < count && e - k < 32 && ns[e] == n) ++e;
+        WorkItem it = make_item(offset[(size_t)k], k, n);
+        it.split = kTinyItem;
+        it.NB = (unsigned long long)(e - k);
+        plan.items[0].push_back(it);
+        k = e - 1;
+    }
+
+    // the other matrices, per class, largest first (ties in matrix order)
+    std::vector<int64_t> order[2];
+    for (int64_t k = 0; k < count; ++k)
+        if (ns[k] > tiny) order[ns[k] <= 32 ? 0 : 1].push_back(k);
+    for (int cls = 0; cls < 2; ++cls) {
+        std::vector<int64_t>& ord = order[cls];
+        std::stable_sort(ord.begin(), ord.end(), [&](int64_t x, int64_t y) { return ns[x] > ns[y]; });
+        const int U = Ucls[cls];
+        // work from each matrix to the end of the order (guided split)
+        std::vector<double> rest(ord.size() + 1, 0.0);
+        for (size_t q = ord.size(); q-- > 0;) rest[q] = rest[q + 1] + std::ldexp(1.0, ns[ord[q]]);
+        const int lo = std::max(kMinChunkLog2, U + 5);
+        const double div = (double)std::max(1, warps ? warps[cls] : 1) * (double)tune.items_per_warp;
+        for (size_t q = 0; q < ord.size(); ++q) {
+            const int64_t k = ord[q];
+            const int n = ns[k];
+            WorkItem it = make_item(offset[(size_t)k], k, n);
+            if (n < U + 1) {
+                it.NB = 0;  // generic walk by one lane
+                plan.items[cls].push_back(it);
+                continue;
+            }
+            const uint64_t NB = (n == 64) ? (1ull << (64 - U)) : (1ull << (n - U));
+            // piece length: fixed, or the work left from here on over
+            // (warps x items_per_warp), so pieces shrink toward the end
+            int cl;
+            if (tune.chunk_log2 > 0) cl = n > tune.cutoff ? tune.chunk_log2 : n;
+            else cl = std::max(lo, floor_log2(rest[q] / div));
+            if (q == 0) plan.chunk_log2[cls] = std::min(cl, n);
+            if (cl >= n) {
+                it.NB = NB;
+                plan.items[cls].push_back(it);
+                continue;
+            }
+            // at most 2^20 items per matrix keeps the item table small for n near 64
+            cl = std::max(std::max(cl, U + 5), n - 20);
+            const uint64_t per = 1ull << (cl - U);
+            const uint64_t nitems = (NB + per - 1) / per;
+            it.split = plan.num_split++;
+            plan.split_items.push_back((unsigned)nitems);
+            for (uint64_t b0 = 0; b0 < NB; b0 += per) {
+                it.B0 = b0;
+                it.NB = std::min<unsigned long long>(per, NB - b0);
+                plan.items[cls].push_back(it);
+            }
+        }
+    }
+    // largest first (longest-processing-time order); ties keep plan order.
+    // Cost = warp time in units of one Gray index of the grouped walk: a
+    // packed lane walks each index about four times slower than the 32 lanes
+    // of a warp walk theirs, so a packed item costs about 2^n x 128.
     for (int cls = 0; cls < 2; ++cls) {
         const int U = Ucls[cls];
         auto cost = [U](const WorkItem& x) -> unsigned long long {
-            if (x.split == kTinyItem || x.NB == 0) return 1ull << x.n;
+            if (x.split == kTinyItem) return (1ull << x.n) << 7;
+            if (x.NB == 0) return 1ull << x.n;
             return (unsigned long long)x.NB << U;
         };
         std::stable_sort(plan.items[cls].begin(), plan.items[cls].end(),
                          [&](const WorkItem& x, const WorkItem& y) { return cost(x) > cost(y); });
     }
+}
+
+void batch_warps(DeviceCtx* c, const BatchTuning& tune, int warps[2])
+{
+    for (int cls = 0; cls < 2; ++cls)
+        warps[cls] = c->sm_count * batch_ctas(c, cls + 1, tune.variant[cls]) * (kBatchThreads / 32);
 }
 
 // grow-only device scratch for a plan
@@ -432,8 +478,8 @@ static void free_graph(BatchGraphCache& g)
 
 static bool same_tuning(const BatchTuning& a, const BatchTuning& b)
 {
-    return a.cutoff == b.cutoff && a.chunk_log2 == b.chunk_log2 && a.variant[0] == b.variant[0] &&
-           a.variant[1] == b.variant[1];
+    return a.tiny_cutoff == b.tiny_cutoff && a.cutoff == b.cutoff && a.chunk_log2 == b.chunk_log2 &&
+           a.items_per_warp == b.items_per_warp && a.variant[0] == b.variant[0] && a.variant[1] == b.variant[1];
 }
 
 // Replay the captured launch sequence when nothing changed, else plan,
@@ -450,7 +496,9 @@ int enqueue_batch_graph(DeviceCtx* c, const int32_t* ns, int64_t count, const ui
     if (e != cudaSuccess) return cuda_rc(e);
     if (g.valid || g.exec) free_graph(g);
     BatchPlan plan;
-    plan_batch(ns, count, c->tune, plan);
+    int warps[2];
+    batch_warps(c, c->tune, warps);
+    plan_batch(ns, count, c->tune, warps, plan);
     const size_t n0 = plan.items[0].size(), n1 = plan.items[1].size();
     const size_t ns_split = (size_t)plan.num_split + 1;
     bool ok = cudaMallocHost(&g.h_items, std::max<size_t>(1, n0 + n1) * sizeof(WorkItem)) == cudaSuccess;
@@ -506,6 +554,53 @@ using namespace pf3;
 
 extern "C" {
 
+int pf3_batch_plan(const int32_t* ns, int64_t count, int tiny_cutoff, int split_cutoff, int chunk_log2,
+                   int items_per_warp, const int* variant, const int* warps, pf3_plan_item* items, int64_t capacity,
+                   int64_t* num_items, int* auto_chunk_log2)
+{
+    if (count < 0 || (count > 0 && !ns) || !variant || !warps || !num_items || capacity < 0) return PF3_EINVAL;
+    if (tiny_cutoff < 0 || tiny_cutoff > kTinyMaxN || split_cutoff < 0 || split_cutoff > PF3_MAX_N ||
+        (chunk_log2 != 0 && (chunk_log2 < 12 || chunk_log2 > 62)) || items_per_warp < 1 || items_per_warp > 1024)
+        return PF3_EINVAL;
+    for (int cls = 0; cls < 2; ++cls)
+        if (variant[cls] < 0 || variant[cls] >= kNumBatchVariants || warps[cls] < 1) return PF3_EINVAL;
+    for (int64_t k = 0; k < count; ++k)
+        if (ns[k] < 0 || ns[k] > PF3_MAX_N) return PF3_EINVAL;
+    BatchTuning t;
+    t.tiny_cutoff = tiny_cutoff;
+    t.cutoff = split_cutoff;
+    t.chunk_log2 = chunk_log2;
+    t.items_per_warp = items_per_warp;
+    t.variant[0] = variant[0];
+    t.variant[1] = variant[1];
+    BatchPlan plan;
+    const int w[2] = {warps[0], warps[1]};
+    plan_batch(ns, count, t, w, plan);
+    const int64_t total = (int64_t)(plan.items[0].size() + plan.items[1].size());
+    *num_items = total;
+    if (auto_chunk_log2) {
+        auto_chunk_log2[0] = plan.chunk_log2[0];
+        auto_chunk_log2[1] = plan.chunk_log2[1];
+    }
+    if (!items) return PF3_OK;
+    if (capacity < total) return PF3_ETOOBIG;
+    int64_t o = 0;
+    for (int cls = 1; cls >= 0; --cls) {
+        const int U = kBatchVariants[variant[cls]].U;
+        for (const WorkItem& it : plan.items[cls]) {
+            pf3_plan_item& x = items[o++];
+            x.mat = it.mat;
+            x.n = it.n;
+            x.kind = it.split == kTinyItem ? 2 : (it.NB == 0 ? 3 : (it.split >= 0 ? 1 : 0));
+            x.first_block = it.B0;
+            x.num_blocks = it.NB;
+            x.block_log2 = U;
+            x.cls = cls;
+        }
+    }
+    return PF3_OK;
+}
+
 int perm_f3_batch(const uint8_t* As, const int32_t* ns, int64_t count, uint8_t* results, uint64_t* hist)
 {
     if (count < 0 || (count > 0 && (!ns || !results))) return PF3_EINVAL;
@@ -526,7 +621,9 @@ int perm_f3_batch(const uint8_t* As, const int32_t* ns, int64_t count, uint8_t* 
     if (!c) return rc;
     std::lock_guard<std::mutex> g(c->mu);
     BatchPlan plan;
-    plan_batch(ns, count, c->tune, plan);
+    int warps[2];
+    batch_warps(c, c->tune, warps);
+    plan_batch(ns, count, c->tune, warps, plan);
     if ((rc = ensure_batch_scratch(c, plan.items[0].size() + plan.items[1].size(), (size_t)plan.num_split, bytes,
                                    (size_t)count)))
         return rc;

@@ -65,9 +65,9 @@ DeviceCtx* device_ctx(int* rc)
     ok = ok && cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) == cudaSuccess;
     ok = ok && cudaMalloc(&c->d_A, kMaxNN) == cudaSuccess;
     ok = ok && cudaMalloc(&c->d_partials, sizeof(unsigned long long) * 2 * (size_t)max_grid) == cudaSuccess;
-    ok = ok && cudaMalloc(&c->d_flags, sizeof(unsigned int) * 2) == cudaSuccess;
+    ok = ok && cudaMalloc(&c->d_flags, sizeof(unsigned int) * 4) == cudaSuccess;
     ok = ok && cudaMalloc(&c->d_out, sizeof(unsigned long long) * 4) == cudaSuccess;
-    ok = ok && cudaMemset(c->d_flags, 0, sizeof(unsigned int) * 2) == cudaSuccess;
+    ok = ok && cudaMemset(c->d_flags, 0, sizeof(unsigned int) * 4) == cudaSuccess;
     ok = ok && cudaMallocHost(&c->h_A, kMaxNN) == cudaSuccess;
     ok = ok && cudaMallocHost(&c->h_out, sizeof(unsigned long long) * 4) == cudaSuccess;
     ok = ok && cudaDeviceSynchronize() == cudaSuccess;
@@ -106,8 +106,9 @@ int enqueue_range(DeviceCtx* c, const uint8_t* dA, int n, uint64_t first, uint64
     a.partials = c->d_partials;
     a.ticket = c->d_flags;
     a.err = c->d_flags + 1;
+    a.cursor = c->d_flags + 2;
     a.out = d_out;
-    const int grid = single_grid_for(a, c->sm_count, single_ctas(c, W, v));
+    const int grid = single_grid_for(a, v, c->sm_count, single_ctas(c, W, v));
     return cuda_rc(launch_single(a, v, grid, stream));
 }
 

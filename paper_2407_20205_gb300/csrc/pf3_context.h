@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "pf3_batch.h"
+#include "pf3_internal.h"
 
 namespace pf3 {
 
@@ -53,14 +54,14 @@ struct DeviceCtx {
     int device = 0;
     int sm_count = 0;
     int single_variant[2] = {0, 0};  // tuned single-kernel variant for W = 1 / W = 2
-    int single_ctas[2][8] = {};      // resident CTAs per SM by W and variant (0 = not queried)
-    int batch_ctas_cache[2][8] = {};
+    int single_ctas[2][kMaxVariants] = {};  // resident CTAs per SM by W and variant (0 = not queried)
+    int batch_ctas_cache[2][kMaxVariants] = {};
     int max_grid = 0;
     cudaStream_t stream = nullptr;
     // single-matrix scratch
     uint8_t* d_A = nullptr;                   // kMaxNN bytes
     unsigned long long* d_partials = nullptr; // 2 * max_grid
-    unsigned int* d_flags = nullptr;          // ticket, error flag (0 between launches)
+    unsigned int* d_flags = nullptr;          // ticket, error flag, chunk cursor (0 between launches)
     unsigned long long* d_out = nullptr;      // plus, minus, result
     uint8_t* h_A = nullptr;                   // pinned
     unsigned long long* h_out = nullptr;      // pinned

@@ -144,6 +144,22 @@ __device__ __forceinline__ State<W> seed_state(const RowTable<W>& tab, int n, ui
     return st;
 }
 
+// the low word (columns 0..31) of seed_state: all the grouped walk carries
+template <int W>
+__device__ __forceinline__ void seed_low(const RowTable<W>& tab, int n, uint64_t i, uint32_t& m, uint32_t& sg)
+{
+    const State<W> init = initial_state<W>(n);
+    m = init.m[0];
+    sg = init.s[0];
+    uint64_t g = i ^ (i >> 1);
+    while (g) {
+        const int r = __ffsll((long long)g) - 1;
+        const RowEntry<W>& e = tab.e[0][r];
+        add_word(m, sg, e.k1[0], e.k2[0]);
+        g &= g - 1;
+    }
+}
+
 template <int W>
 __device__ __forceinline__ bool all_ones(const State<W>& st)
 {
@@ -373,11 +389,7 @@ __device__ __forceinline__ void walk_groups(const RowTable<W>& tab, const GroupR
                                             uint64_t len, uint64_t trip, WarpQueue& q, int lane, Counts& c)
 {
     uint32_t m = 0, sg = 0;  // low word of the base state
-    if (len) {
-        const State<W> st = seed_state<W>(tab, n, B0 << U);
-        m = st.m[0];
-        sg = st.s[0];
-    }
+    if (len) seed_low<W>(tab, n, B0 << U, m, sg);
     for (uint64_t it = 0; it < trip; ++it) {
         if (it < len) {
             const uint64_t B = B0 + it;

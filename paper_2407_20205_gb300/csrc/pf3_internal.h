@@ -7,22 +7,24 @@
 
 namespace pf3 {
 
-constexpr int kSingleThreads = 256;
-
 // A compiled variant of a walk kernel: probe groups of 2^G Gray indices,
-// unrolled blocks of 2^U indices, and the minimum resident CTAs per SM it was
-// compiled for (its register budget).
+// unrolled blocks of 2^U indices, the minimum resident CTAs per SM it was
+// compiled for (its register budget) and its CTA size.
 struct KernelVariant {
     int U;
     int G;
     int min_ctas;
+    int threads;
 };
-constexpr int kNumSingleVariants = 7;
-constexpr KernelVariant kSingleVariants[kNumSingleVariants] = {{9, 5, 2}, {9, 4, 2}, {8, 4, 2}, {10, 5, 2},
-                                                               {8, 5, 2}, {9, 5, 3}, {9, 5, 1}};
+constexpr int kMaxVariants = 16;
+constexpr int kNumSingleVariants = 8;
+constexpr KernelVariant kSingleVariants[kNumSingleVariants] = {{9, 5, 2, 256}, {9, 4, 2, 256}, {8, 4, 2, 256},
+                                                               {10, 5, 2, 256}, {8, 5, 2, 256}, {9, 5, 3, 256},
+                                                               {9, 5, 1, 256}, {9, 5, 4, 128}};
 constexpr int kNumBatchVariants = 6;
-constexpr KernelVariant kBatchVariants[kNumBatchVariants] = {{9, 5, 4}, {9, 4, 4}, {8, 4, 4}, {9, 5, 2},
-                                                             {10, 5, 2}, {8, 5, 4}};
+constexpr KernelVariant kBatchVariants[kNumBatchVariants] = {{9, 5, 4, 128}, {9, 4, 4, 128}, {8, 4, 4, 128},
+                                                             {9, 5, 2, 128}, {10, 5, 2, 128}, {8, 5, 4, 128}};
+static_assert(kNumSingleVariants <= kMaxVariants && kNumBatchVariants <= kMaxVariants, "variant tables");
 
 // One range job for the single-matrix kernel; all indices are Gray indices.
 struct SingleArgs {
@@ -34,9 +36,21 @@ struct SingleArgs {
     uint64_t tail_first, tail_last;
     uint64_t mid_B0;         // aligned blocks [mid_B0, mid_B0 + mid_NB)
     uint64_t mid_NB;
+    // The middle blocks are handed to warps in chunks through an atomic
+    // cursor, in guided phases: phase j is per_phase chunks of len0 >> j
+    // blocks (while that is at least tail_len), then chunks of tail_len
+    // blocks cover the rest up to mid_NB; nchunks in all.  Each phase takes
+    // about half of what is left, so warps that run ahead take more and all
+    // finish together.  Set by launch_single from the grid size.
+    // With dynamic == 0 each thread walks one contiguous share of the middle
+    // blocks instead and the cursor is not used.
+    uint64_t len0, tail_len;
+    unsigned per_phase, nchunks;
+    int dynamic;
     unsigned long long* partials;  // device scratch, 2 per CTA
     unsigned int* ticket;          // device scratch, 0 between launches
     unsigned int* err;             // device scratch, 0 between launches
+    unsigned int* cursor;          // device scratch, 0 between launches
     unsigned long long* out;       // device: plus, minus, result (~0 on bad entry)
 };
 
@@ -44,11 +58,17 @@ struct SingleArgs {
 // indices and a ragged tail
 void plan_range(int n, uint64_t first, uint64_t last, int U, SingleArgs& a);
 
-// launch variant `v` of the single-matrix walk (W = 1 for n <= 32, else 2)
+// split the middle blocks into the chunks warps take from the cursor, for
+// `grid` CTAs of `threads` threads
+void plan_chunks(SingleArgs& a, int grid, int threads);
+
+// launch variant `v` of the single-matrix walk (W = 1 for n <= 32, else 2);
+// plans the chunks for `grid` CTAs
 cudaError_t launch_single(const SingleArgs& a, int v, int grid, cudaStream_t stream);
 
-// CTAs to launch for this plan given the device (one resident wave at most)
-int single_grid_for(const SingleArgs& a, int sm_count, int max_ctas_per_sm);
+// CTAs of variant v to launch for this plan given the device (one resident
+// wave at most)
+int single_grid_for(const SingleArgs& a, int v, int sm_count, int max_ctas_per_sm);
 
 // resident CTAs per SM of variant v of the single-matrix kernel for W
 int single_max_ctas_per_sm(int W, int v);

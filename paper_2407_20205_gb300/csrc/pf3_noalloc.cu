@@ -7,15 +7,16 @@
 // may synchronise the device and stall every stream) is not acceptable.  This
 // file gives them perm_f3_range_counts_noalloc: the same walk as
 // perm_f3_range_counts_async, with the kernel's scratch (one pair of partial
-// counts per CTA, the last-CTA ticket and the error flag) in a fixed
-// file-scope device array instead of memory the library allocates.  The
-// caller still owns and passes the matrix and the output buffer.
+// counts per CTA, the last-CTA ticket, the error flag and the chunk cursor)
+// in a fixed file-scope device array instead of memory the library
+// allocates.  The caller still owns and passes the matrix and the output
+// buffer.
 //
 // The array is part of the module: every GPU that loads the library holds its
 // PF3_NOALLOC_MAX_CTAS * 16 + 256 bytes until the process exits.  All calls on
 // a device share it and it keeps the last call's contents, so each call first
-// clears the ticket and error flag (cudaMemsetAsync, no allocation), and two
-// calls that overlap on the GPU race on it.
+// clears the ticket, error flag and cursor (cudaMemsetAsync, no allocation),
+// and two calls that overlap on the GPU race on it.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -31,7 +32,7 @@ namespace {
 constexpr int kNoAllocFlagsBytes = 256;
 constexpr size_t kNoAllocBytes = (size_t)PF3_NOALLOC_MAX_CTAS * 2 * sizeof(unsigned long long) + kNoAllocFlagsBytes;
 
-// flags first (ticket, error), then 2 x uint64 per CTA
+// flags first (ticket, error, chunk cursor), then 2 x uint64 per CTA
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 constexpr int kMaxDevices = 64;
@@ -85,13 +86,14 @@ extern "C" int perm_f3_range_counts_noalloc(const uint8_t* dA, int n, uint64_t f
     a.A = dA;
     a.ticket = (unsigned int*)base;
     a.err = (unsigned int*)base + 1;
+    a.cursor = (unsigned int*)base + 2;
     a.partials = (unsigned long long*)(base + kNoAllocFlagsBytes);
     a.out = (unsigned long long*)d_out;
-    int grid = single_grid_for(a, g_noalloc_sms[dev], g_noalloc_ctas[dev][W - 1]);
+    int grid = single_grid_for(a, v, g_noalloc_sms[dev], g_noalloc_ctas[dev][W - 1]);
     if (ctas > 0 && grid > ctas) grid = ctas;
     if (grid > PF3_NOALLOC_MAX_CTAS) grid = PF3_NOALLOC_MAX_CTAS;
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = cudaMemsetAsync(base, 0, 2 * sizeof(unsigned int), s);
+    cudaError_t e = cudaMemsetAsync(base, 0, 3 * sizeof(unsigned int), s);
     if (e == cudaSuccess) e = launch_single(a, v, grid, s);
     return e == cudaSuccess ? PF3_OK : PF3_ECUDA;
 }

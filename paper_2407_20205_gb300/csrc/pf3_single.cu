@@ -3,12 +3,17 @@
 //
 // Sec. 3.1 of the paper splits the 2^n Gray states into blocks of consecutive
 // states, each started by jumping to gray(start).  Here a block is 2^U
-// consecutive indices (U picked by the autotuner); thread k of the grid walks a
-// contiguous run of blocks, seeded once by a direct subset sum.  Each CTA
-// packs the matrix into a shared-memory row table itself (no separate pack
-// launch), the per-thread (+1, -1) term counts are reduced by warp shuffles
-// and shared memory, and the last CTA to finish adds the per-CTA partials and
-// maps the counts to perm mod 3.
+// consecutive indices (U picked by the autotuner).  In a short launch each
+// thread walks one contiguous run of blocks, seeded once by a direct subset
+// sum.  In a long one a warp takes chunks of consecutive blocks from an
+// atomic cursor (each lane a contiguous run of the chunk); chunks are long at
+// first and short at the end, so warps that the schedulers favour take more
+// of them and the SMs' pipes stay full until the last chunk (with fixed
+// shares about a quarter of the warps sat idle at the end).
+// Each CTA packs the matrix into a shared-memory row table itself (no
+// separate pack launch), the per-thread (+1, -1) term counts are reduced by
+// warp shuffles and shared memory, and the last CTA to finish adds the
+// per-CTA partials and maps the counts to perm mod 3.
 #include <cuda_runtime.h>
 
 #include "pf3_device.cuh"
@@ -18,18 +23,39 @@ namespace pf3 {
 
 namespace {
 
-template <int W, int U, int G, int MINB>
-__global__ void __launch_bounds__(kSingleThreads, MINB) single_kernel(SingleArgs a)
+// chunk k < nchunks of the middle blocks (relative to mid_B0): see
+// SingleArgs.  At most one turn per guided phase (the length halves each turn).
+__device__ __forceinline__ void chunk_range(const SingleArgs& a, unsigned k, uint64_t& start, uint64_t& len)
+{
+    uint64_t s = 0, L = a.len0;
+    while (L >= a.tail_len) {
+        if (k < a.per_phase) {
+            start = s + (uint64_t)k * L;
+            const uint64_t left = a.mid_NB - start;
+            len = left < L ? left : L;
+            return;
+        }
+        s += (uint64_t)a.per_phase * L;
+        k -= a.per_phase;
+        L = (L >> 1) & ~31ull;
+    }
+    start = s + (uint64_t)k * a.tail_len;
+    const uint64_t left = a.mid_NB - start;
+    len = left < a.tail_len ? left : a.tail_len;
+}
+
+template <int W, int U, int G, int MINB, int THREADS>
+__global__ void __launch_bounds__(THREADS, MINB) single_kernel(SingleArgs a)
 {
     __shared__ RowTable<W> tab;
-    __shared__ WarpQueue queues[kSingleThreads / 32];
-    __shared__ unsigned long long red[2][kSingleThreads / 32];
+    __shared__ WarpQueue queues[THREADS / 32];
+    __shared__ unsigned long long red[2][THREADS / 32];
     __shared__ bool s_last;
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     if (lane == 0) queues[warp].count = 0;
-    const bool bad_local = build_row_table<W>(tab, a.A, a.n, warp, kSingleThreads / 32, lane);
+    const bool bad_local = build_row_table<W>(tab, a.A, a.n, warp, THREADS / 32, lane);
     const bool bad = __syncthreads_or(bad_local) != 0;
 
     Counts c{0ull, 0ull};
@@ -39,10 +65,27 @@ __global__ void __launch_bounds__(kSingleThreads, MINB) single_kernel(SingleArgs
         if (a.mid_NB) {
             GroupRows<G, U> R;
             load_group_rows<W, G, U>(R, tab);
-            uint64_t s, len;
-            split_range(a.mid_NB, T, tid, s, len);
-            const uint64_t trip = __shfl_sync(0xFFFFFFFFu, len, 0);  // lane 0 holds the longest share
-            walk_groups<W, G, U>(tab, R, a.n, a.mid_B0 + s, len, trip, queues[warp], lane, c);
+            if (!a.dynamic) {
+                // one contiguous share of the blocks per thread
+                uint64_t s, len;
+                split_range(a.mid_NB, T, tid, s, len);
+                const uint64_t trip = __shfl_sync(0xFFFFFFFFu, len, 0);  // lane 0 holds the longest share
+                walk_groups<W, G, U>(tab, R, a.n, a.mid_B0 + s, len, trip, queues[warp], lane, c);
+            } else {
+                // the cursor only grows, and every chunk index at or past
+                // nchunks ends the loop: at most nchunks + 1 turns per warp
+                for (;;) {
+                    unsigned k = 0;
+                    if (lane == 0) k = atomicAdd(a.cursor, 1u);
+                    k = __shfl_sync(0xFFFFFFFFu, k, 0);
+                    if (k >= a.nchunks) break;
+                    uint64_t cs, clen, s, len;
+                    chunk_range(a, k, cs, clen);
+                    split_range(clen, 32, (uint64_t)lane, s, len);
+                    const uint64_t trip = __shfl_sync(0xFFFFFFFFu, len, 0);
+                    walk_groups<W, G, U>(tab, R, a.n, a.mid_B0 + cs + s, len, trip, queues[warp], lane, c);
+                }
+            }
         }
         if (a.has_head && tid == T - 1) walk_generic<W>(tab, a.n, a.head_first, a.head_last, c);
         if (a.has_tail && tid == (T > 1 ? T - 2 : 0)) walk_generic<W>(tab, a.n, a.tail_first, a.tail_last, c);
@@ -58,7 +101,7 @@ __global__ void __launch_bounds__(kSingleThreads, MINB) single_kernel(SingleArgs
     if (threadIdx.x == 0) {
         p = 0;
         m = 0;
-        for (int w = 0; w < kSingleThreads / 32; ++w) {
+        for (int w = 0; w < THREADS / 32; ++w) {
             p += red[0][w];
             m += red[1][w];
         }
@@ -91,7 +134,7 @@ __global__ void __launch_bounds__(kSingleThreads, MINB) single_kernel(SingleArgs
     if (threadIdx.x == 0) {
         p = 0;
         m = 0;
-        for (int w = 0; w < kSingleThreads / 32; ++w) {
+        for (int w = 0; w < THREADS / 32; ++w) {
             p += red[0][w];
             m += red[1][w];
         }
@@ -99,6 +142,8 @@ __global__ void __launch_bounds__(kSingleThreads, MINB) single_kernel(SingleArgs
         a.out[0] = p;
         a.out[1] = m;
         a.out[2] = e ? ~0ull : (unsigned long long)perm_from_counts(a.n, p, m);
+        // every CTA took its last chunk before its ticket
+        *a.cursor = 0u;
         *a.ticket = 0u;
         __threadfence();
     }
@@ -147,13 +192,22 @@ template <int W>
 const void* single_kernel_ptr(int v)
 {
     switch (v) {
-    case 0: return (const void*)single_kernel<W, kSingleVariants[0].U, kSingleVariants[0].G, kSingleVariants[0].min_ctas>;
-    case 1: return (const void*)single_kernel<W, kSingleVariants[1].U, kSingleVariants[1].G, kSingleVariants[1].min_ctas>;
-    case 2: return (const void*)single_kernel<W, kSingleVariants[2].U, kSingleVariants[2].G, kSingleVariants[2].min_ctas>;
-    case 3: return (const void*)single_kernel<W, kSingleVariants[3].U, kSingleVariants[3].G, kSingleVariants[3].min_ctas>;
-    case 4: return (const void*)single_kernel<W, kSingleVariants[4].U, kSingleVariants[4].G, kSingleVariants[4].min_ctas>;
-    case 5: return (const void*)single_kernel<W, kSingleVariants[5].U, kSingleVariants[5].G, kSingleVariants[5].min_ctas>;
-    default: return (const void*)single_kernel<W, kSingleVariants[6].U, kSingleVariants[6].G, kSingleVariants[6].min_ctas>;
+    case 0: return (const void*)single_kernel<W, kSingleVariants[0].U, kSingleVariants[0].G, kSingleVariants[0].min_ctas,
+                                                   kSingleVariants[0].threads>;
+    case 1: return (const void*)single_kernel<W, kSingleVariants[1].U, kSingleVariants[1].G, kSingleVariants[1].min_ctas,
+                                                   kSingleVariants[1].threads>;
+    case 2: return (const void*)single_kernel<W, kSingleVariants[2].U, kSingleVariants[2].G, kSingleVariants[2].min_ctas,
+                                                   kSingleVariants[2].threads>;
+    case 3: return (const void*)single_kernel<W, kSingleVariants[3].U, kSingleVariants[3].G, kSingleVariants[3].min_ctas,
+                                                   kSingleVariants[3].threads>;
+    case 4: return (const void*)single_kernel<W, kSingleVariants[4].U, kSingleVariants[4].G, kSingleVariants[4].min_ctas,
+                                                   kSingleVariants[4].threads>;
+    case 5: return (const void*)single_kernel<W, kSingleVariants[5].U, kSingleVariants[5].G, kSingleVariants[5].min_ctas,
+                                                   kSingleVariants[5].threads>;
+    case 6: return (const void*)single_kernel<W, kSingleVariants[6].U, kSingleVariants[6].G, kSingleVariants[6].min_ctas,
+                                                   kSingleVariants[6].threads>;
+    default: return (const void*)single_kernel<W, kSingleVariants[7].U, kSingleVariants[7].G, kSingleVariants[7].min_ctas,
+                                                   kSingleVariants[7].threads>;
     }
 }
 
@@ -194,24 +248,62 @@ int single_max_ctas_per_sm(int W, int v)
 {
     int ctas = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, W == 1 ? single_kernel_ptr<1>(v) : single_kernel_ptr<2>(v),
-                                                  kSingleThreads, 0);
+                                                  kSingleVariants[v].threads, 0);
     return ctas > 0 ? ctas : 1;
 }
 
-int single_grid_for(const SingleArgs& a, int sm_count, int max_ctas_per_sm)
+int single_grid_for(const SingleArgs& a, int v, int sm_count, int max_ctas_per_sm)
 {
+    const uint64_t threads = (uint64_t)kSingleVariants[v].threads;
     const uint64_t wave = (uint64_t)sm_count * (uint64_t)max_ctas_per_sm;
-    const uint64_t need = (a.mid_NB + kSingleThreads - 1) / kSingleThreads;
+    const uint64_t need = (a.mid_NB + threads - 1) / threads;
     uint64_t g = need < wave ? need : wave;
     if (g < 1) g = 1;
     return (int)g;
 }
 
-cudaError_t launch_single(const SingleArgs& a, int v, int grid, cudaStream_t stream)
+// Work split for `grid` CTAs of `threads` threads (P warps).  Below 512
+// blocks per lane each thread walks one contiguous share (dynamic = 0): the
+// finishing spread of a short launch costs less than re-seeding chunks would.
+// Above, guided chunks, every length a multiple of 32 blocks so the lanes of
+// a warp share a chunk evenly: phase j is 4P chunks of len0 >> j blocks
+// (rounded down to 32), len0 = mid_NB / 8P, so each phase takes half of what
+// is left and the phases cover at most mid_NB, while that length is at least
+// 128 blocks; tail chunks of 128 blocks (4 per lane) cover the rest.
+void plan_chunks(SingleArgs& a, int grid, int threads)
 {
+    const uint64_t P = (uint64_t)(grid > 0 ? grid : 1) * (uint64_t)(threads / 32);
+    const uint64_t NB = a.mid_NB;
+    if (NB < P * 32 * 512) {
+        a.len0 = a.tail_len = 0;
+        a.per_phase = a.nchunks = 0;
+        a.dynamic = 0;
+        return;
+    }
+    const uint64_t tl = 128;
+    const uint64_t per = 4 * P;
+    const uint64_t L0 = (NB / (8 * P)) & ~31ull;                // >= 2048
+    uint64_t used = 0, chunks = 0;
+    for (uint64_t L = L0; L >= tl; L = (L >> 1) & ~31ull) {
+        used += per * L;
+        chunks += per;
+    }
+    chunks += (NB - used + tl - 1) / tl;
+    a.len0 = L0;
+    a.tail_len = tl;
+    a.per_phase = (unsigned)per;
+    a.nchunks = (unsigned)chunks;
+    a.dynamic = 1;
+}
+
+cudaError_t launch_single(const SingleArgs& args, int v, int grid, cudaStream_t stream)
+{
+    SingleArgs a = args;
+    const int threads = kSingleVariants[v].threads;
+    plan_chunks(a, grid, threads);
     const void* fn = a.n <= 32 ? single_kernel_ptr<1>(v) : single_kernel_ptr<2>(v);
-    void* args[] = {(void*)&a};
-    return cudaLaunchKernel(fn, dim3(grid), dim3(kSingleThreads), args, 0, stream);
+    void* kargs[] = {(void*)&a};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(threads), kargs, 0, stream);
 }
 
 cudaError_t launch_step_table(uint32_t* out, cudaStream_t stream)

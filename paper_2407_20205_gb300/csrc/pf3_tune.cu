@@ -3,9 +3,12 @@
 // Each walk kernel is compiled in a few variants (unrolled block length 2^U,
 // register budget).  The autotuner times every variant of the single-matrix
 // kernel and of the batch kernel on the current device, separately for one
-// and two words per plane, and keeps the fastest; the batch split length is
-// chosen on a mixed-size sample.  Sample matrices come from a fixed xorshift
-// stream (uniform entries in {0,1,2}).
+// and two words per plane, and keeps the fastest.  It then picks the batch
+// packing cutoff (up to which n matrices are walked one per lane, 32 per
+// warp) by timing both walks per n, and the batch split granularity (split
+// items per warp, which sets the item length and so how many warps share one
+// matrix) on mixed-size batches.  Sample matrices come from fixed xorshift
+// streams (uniform entries in {0,1,2}).
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -39,6 +42,25 @@ void sample_matrix(uint8_t* A, int n, uint64_t seed)
     }
 }
 
+// `bytes` uniform entries in {0,1,2} from one stream (any n x n slice of it
+// is a uniform matrix)
+void fill_uniform(uint8_t* out, size_t bytes, uint64_t seed)
+{
+    uint64_t x = seed * 0x9E3779B97F4A7C15ull + 1;
+    for (size_t k = 0; k < bytes;) {
+        x ^= x << 13;
+        x ^= x >> 7;
+        x ^= x << 17;
+        for (int f = 0; f < 32 && k < bytes; ++f) {
+            const unsigned v = (unsigned)(x >> (2 * f)) & 3u;
+            if (v < 3) out[k++] = (uint8_t)v;
+        }
+    }
+}
+
+constexpr int kSplitCandidates = PF3_SPLIT_CANDIDATES;  // items per warp 1, 2, 4, 8, 16
+static_assert(kTinyMaxN == PF3_TINY_MAX_N, "packing capacity");
+
 // average milliseconds of `reps` launches of fn after one warm-up
 template <class F>
 float time_ms(cudaStream_t s, int reps, F fn)
@@ -62,7 +84,9 @@ float time_ms(cudaStream_t s, int reps, F fn)
 
 // Autotune cache: a text file named by the environment variable
 // PF3_TUNE_CACHE, one line per GPU model:
-//   <device name>|<SM count>|<single W=1>|<single W=2>|<batch W=1>|<batch W=2>
+//   <device name>|<SM count>|<single W=1>|<single W=2>|<batch W=1>|<batch W=2>|
+//   <packing cutoff>|<split items per warp>
+// (lines without the last two fields set only the variants).
 static std::string tune_key(int device)
 {
     cudaDeviceProp prop;
@@ -84,15 +108,23 @@ void load_tune_cache(DeviceCtx* c)
     while (std::fgets(line, sizeof(line), f)) {
         std::string l(line);
         if (l.compare(0, key.size(), key) != 0 || l.size() <= key.size() || l[key.size()] != '|') continue;
-        int v[4];
-        if (std::sscanf(l.c_str() + key.size() + 1, "%d|%d|%d|%d", &v[0], &v[1], &v[2], &v[3]) != 4) continue;
+        int v[6];
+        const int got = std::sscanf(l.c_str() + key.size() + 1, "%d|%d|%d|%d|%d|%d", &v[0], &v[1], &v[2], &v[3],
+                                    &v[4], &v[5]);
+        if (got != 4 && got != 6) continue;
         if (v[0] < 0 || v[0] >= kNumSingleVariants || v[1] < 0 || v[1] >= kNumSingleVariants || v[2] < 0 ||
             v[2] >= kNumBatchVariants || v[3] < 0 || v[3] >= kNumBatchVariants)
             continue;
+        if (got == 6 && (v[4] < 0 || v[4] > kTinyMaxN || v[5] < 1 || v[5] > 1024)) continue;
         c->single_variant[0] = v[0];
         c->single_variant[1] = v[1];
         c->tune.variant[0] = v[2];
         c->tune.variant[1] = v[3];
+        if (got == 6) {
+            c->tune.tiny_cutoff = v[4];
+            c->tune.items_per_warp = v[5];
+            c->tune.chunk_log2 = 0;
+        }
     }
     std::fclose(f);
 }
@@ -115,8 +147,8 @@ static void store_tune_cache(DeviceCtx* c)
     FILE* f = std::fopen(tmp.c_str(), "w");
     if (!f) return;
     for (const auto& l : keep) std::fputs(l.c_str(), f);
-    std::fprintf(f, "%s|%d|%d|%d|%d\n", key.c_str(), c->single_variant[0], c->single_variant[1], c->tune.variant[0],
-                 c->tune.variant[1]);
+    std::fprintf(f, "%s|%d|%d|%d|%d|%d|%d\n", key.c_str(), c->single_variant[0], c->single_variant[1],
+                 c->tune.variant[0], c->tune.variant[1], c->tune.tiny_cutoff, c->tune.items_per_warp);
     std::fclose(f);
     std::rename(tmp.c_str(), path);
 }
@@ -161,6 +193,13 @@ int pf3_variant_info(int which, int v, int* U, int* G, int* min_ctas)
     return PF3_OK;
 }
 
+int pf3_variant_threads(int which, int v)
+{
+    if (which == 0 && v >= 0 && v < kNumSingleVariants) return kSingleVariants[v].threads;
+    if (which == 1 && v >= 0 && v < kNumBatchVariants) return kBatchVariants[v].threads;
+    return PF3_EINVAL;
+}
+
 int pf3_get_variant(int which, int W)
 {
     if (W < 1 || W > 2 || which < 0 || which > 1) return PF3_EINVAL;
@@ -172,7 +211,8 @@ int pf3_get_variant(int which, int W)
 
 int pf3_set_batch_split(int cutoff, int chunk_log2)
 {
-    if (cutoff < 0 || cutoff > PF3_MAX_N || chunk_log2 < 12 || chunk_log2 > 62) return PF3_EINVAL;
+    if (cutoff < 0 || cutoff > PF3_MAX_N || (chunk_log2 != 0 && (chunk_log2 < 12 || chunk_log2 > 62)))
+        return PF3_EINVAL;
     int rc;
     DeviceCtx* c = device_ctx(&rc);
     if (!c) return rc;
@@ -182,7 +222,36 @@ int pf3_set_batch_split(int cutoff, int chunk_log2)
     return PF3_OK;
 }
 
-int pf3_autotune(double* single_ms, double* batch_ms)
+int pf3_set_batch_tuning(int tiny_cutoff, int split_cutoff, int chunk_log2, int items_per_warp)
+{
+    if (tiny_cutoff < 0 || tiny_cutoff > kTinyMaxN || split_cutoff < 0 || split_cutoff > PF3_MAX_N ||
+        (chunk_log2 != 0 && (chunk_log2 < 12 || chunk_log2 > 62)) || items_per_warp < 1 || items_per_warp > 1024)
+        return PF3_EINVAL;
+    int rc;
+    DeviceCtx* c = device_ctx(&rc);
+    if (!c) return rc;
+    std::lock_guard<std::mutex> g(c->mu);
+    c->tune.tiny_cutoff = tiny_cutoff;
+    c->tune.cutoff = split_cutoff;
+    c->tune.chunk_log2 = chunk_log2;
+    c->tune.items_per_warp = items_per_warp;
+    return PF3_OK;
+}
+
+int pf3_get_batch_tuning(int* tiny_cutoff, int* split_cutoff, int* chunk_log2, int* items_per_warp)
+{
+    int rc;
+    DeviceCtx* c = device_ctx(&rc);
+    if (!c) return rc;
+    std::lock_guard<std::mutex> g(c->mu);
+    if (tiny_cutoff) *tiny_cutoff = c->tune.tiny_cutoff;
+    if (split_cutoff) *split_cutoff = c->tune.cutoff;
+    if (chunk_log2) *chunk_log2 = c->tune.chunk_log2;
+    if (items_per_warp) *items_per_warp = c->tune.items_per_warp;
+    return PF3_OK;
+}
+
+int pf3_autotune_ex(double* single_ms, double* batch_ms, double* pack_ms, double* split_ms)
 {
     int rc;
     DeviceCtx* c = device_ctx(&rc);
@@ -220,11 +289,12 @@ int pf3_autotune(double* single_ms, double* batch_ms)
         }
         c->single_variant[W - 1] = bestv;
     }
-    // ---- batch kernel: 3072 whole matrices of n = 24 (W = 1); 20 matrices of
-    // n = 33 cut into split items (W = 2)
+    // ---- batch kernel variants: 3072 whole matrices of n = 24 (W = 1); 20
+    // matrices of n = 33 cut into split items (W = 2)
+    int warps[2];
     const int bn[2] = {24, 33};
     const int bcount[2] = {3072, 20};
-    for (int W = 1; W <= 2; ++W) {
+    for (int W = 1; W <= 2 && e == cudaSuccess; ++W) {
         const int n = bn[W - 1], cnt = bcount[W - 1];
         std::vector<int32_t> ns(cnt, n);
         std::vector<uint8_t> hAs((size_t)cnt * n * n);
@@ -233,17 +303,21 @@ int pf3_autotune(double* single_ms, double* batch_ms)
         uint8_t* dres = nullptr;
         e = cudaMalloc(&dAs, hAs.size());
         if (e == cudaSuccess) e = cudaMalloc(&dres, cnt);
-        if (e != cudaSuccess) break;
+        if (e != cudaSuccess) {
+            cudaFree(dAs);
+            break;
+        }
         cudaMemcpy(dAs, hAs.data(), hAs.size(), cudaMemcpyHostToDevice);
         const BatchTuning keep = c->tune;
-        if (W == 1) c->tune.cutoff = PF3_MAX_N;  // whole matrices per warp
-        else c->tune.cutoff = 28, c->tune.chunk_log2 = 26;
+        c->tune.chunk_log2 = 26;
+        c->tune.cutoff = (W == 1) ? PF3_MAX_N : 28;  // W = 1: whole matrices per warp
         float best = 1e30f;
         int bestv = 0;
         for (int v = 0; v < kNumBatchVariants; ++v) {
             c->tune.variant[W - 1] = v;
+            batch_warps(c, c->tune, warps);
             BatchPlan plan;
-            plan_batch(ns.data(), cnt, c->tune, plan);
+            plan_batch(ns.data(), cnt, c->tune, warps, plan);
             const float ms = time_ms(s, 1, [&] { enqueue_batch(c, plan, dAs, dres, nullptr, s); });
             if (batch_ms) batch_ms[(W - 1) * kNumBatchVariants + v] = ms;
             if (ms < best) {
@@ -256,12 +330,110 @@ int pf3_autotune(double* single_ms, double* batch_ms)
         cudaFree(dAs);
         cudaFree(dres);
     }
+    batch_warps(c, c->tune, warps);
+
+    // ---- packing cutoff: for each n above the W = 1 variant's block length,
+    // a full grid of n x n matrices (two packed items per warp) walked one
+    // matrix per lane against one matrix per warp; the cutoff is the last n
+    // (counting up) at which the packed walk is faster.  Below U + 1 a warp
+    // would leave all but one lane idle, so packing always wins there.
+    if (pack_ms)
+        for (int k = 0; k < 2 * (kTinyMaxN + 1); ++k) pack_ms[k] = 0.0;
+    if (e == cudaSuccess) {
+        const int U = kBatchVariants[c->tune.variant[0]].U;
+        const int64_t K = (int64_t)warps[0] * 32 * 2;
+        uint8_t* dAs = nullptr;
+        uint8_t* dres = nullptr;
+        const size_t bytes = (size_t)K * kTinyMaxN * kTinyMaxN;
+        e = cudaMalloc(&dAs, bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&dres, (size_t)K);
+        if (e == cudaSuccess) {
+            std::vector<uint8_t> hAs(bytes);
+            fill_uniform(hAs.data(), bytes, 4242);
+            e = cudaMemcpy(dAs, hAs.data(), bytes, cudaMemcpyHostToDevice);
+        }
+        int tiny = std::min(U, kTinyMaxN);
+        const BatchTuning keep = c->tune;
+        for (int n = U + 1; n <= kTinyMaxN && e == cudaSuccess; ++n) {
+            std::vector<int32_t> ns((size_t)K, n);
+            float t[2];
+            for (int path = 0; path < 2; ++path) {
+                c->tune.tiny_cutoff = path == 0 ? n : n - 1;
+                BatchPlan plan;
+                plan_batch(ns.data(), K, c->tune, warps, plan);
+                t[path] = time_ms(s, 1, [&] { enqueue_batch(c, plan, dAs, dres, nullptr, s); });
+                if (pack_ms) pack_ms[path * (kTinyMaxN + 1) + n] = t[path];
+            }
+            if (t[0] >= t[1]) break;
+            tiny = n;
+        }
+        c->tune = keep;
+        c->tune.tiny_cutoff = tiny;
+        cudaFree(dAs);
+        cudaFree(dres);
+    }
+
+    // ---- split granularity: the guided split with 1..16 items per warp,
+    // timed on three batches (3000 x n = 26, where the last partial round
+    // matters; 300 x 28 + 600 x 26 + 1200 x 24; 20 x 33 + 6 x 34, fewer
+    // matrices than warps); the fastest total wins, ties within 1 % going to
+    // fewer, longer items.
+    if (e == cudaSuccess) {
+        const int mixes[3][3][2] = {{{26, 3000}, {0, 0}, {0, 0}},
+                                    {{28, 300}, {26, 600}, {24, 1200}},
+                                    {{33, 20}, {34, 6}, {0, 0}}};
+        std::vector<int32_t> ns[3];
+        size_t bytes[3] = {0, 0, 0}, max_bytes = 0, max_count = 0;
+        for (int w = 0; w < 3; ++w) {
+            for (const auto& m : mixes[w])
+                for (int k = 0; k < m[1]; ++k) {
+                    ns[w].push_back(m[0]);
+                    bytes[w] += (size_t)m[0] * m[0];
+                }
+            max_bytes = std::max(max_bytes, bytes[w]);
+            max_count = std::max(max_count, ns[w].size());
+        }
+        uint8_t* dAs = nullptr;
+        uint8_t* dres = nullptr;
+        e = cudaMalloc(&dAs, max_bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&dres, max_count);
+        if (e == cudaSuccess) {
+            std::vector<uint8_t> hAs(max_bytes);
+            fill_uniform(hAs.data(), max_bytes, 4343);
+            e = cudaMemcpy(dAs, hAs.data(), max_bytes, cudaMemcpyHostToDevice);
+        }
+        const BatchTuning keep = c->tune;
+        c->tune.chunk_log2 = 0;
+        float best = 1e30f;
+        int bestg = keep.items_per_warp;
+        for (int k = 0; k < kSplitCandidates && e == cudaSuccess; ++k) {
+            c->tune.items_per_warp = 1 << k;
+            float ms = 0.f;
+            for (int w = 0; w < 3; ++w) {
+                BatchPlan plan;
+                plan_batch(ns[w].data(), (int64_t)ns[w].size(), c->tune, warps, plan);
+                ms += time_ms(s, 1, [&] { enqueue_batch(c, plan, dAs, dres, nullptr, s); });
+            }
+            if (split_ms) split_ms[k] = ms;
+            if (ms < 0.99f * best) {
+                best = ms;
+                bestg = 1 << k;
+            }
+        }
+        c->tune = keep;
+        c->tune.chunk_log2 = 0;
+        c->tune.items_per_warp = bestg;
+        cudaFree(dAs);
+        cudaFree(dres);
+    }
     cudaFree(dA);
     cudaFree(dout);
-    e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e == cudaSuccess) store_tune_cache(c);
     return cuda_rc(e);
 }
+
+int pf3_autotune(double* single_ms, double* batch_ms) { return pf3_autotune_ex(single_ms, batch_ms, nullptr, nullptr); }
 
 }  // extern "C"

@@ -304,6 +304,7 @@ def test_every_single_variant(pf3, oracle):
 
 def test_every_batch_variant(pf3, oracle):
     keep = {W: pf3.get_variant(pf3.BATCH, W) for W in (1, 2)}
+    keep_tuning = pf3.get_batch_tuning()
     try:
         ns = [5, 9, 13, 17, 20, 22, 3, 12]
         mats = [inputs.uniform_matrix(8100 + k, n) for k, n in enumerate(ns)]
@@ -317,14 +318,45 @@ def test_every_batch_variant(pf3, oracle):
             assert list(pf3.perm_f3_batch(mats)) == want, v
             assert list(pf3.perm_f3_batch(big)) == want_big, v
     finally:
-        pf3.set_batch_split(28, 26)
+        pf3.set_batch_tuning(*keep_tuning.values())
         for W in (1, 2):
             pf3.set_variant(pf3.BATCH, W, keep[W])
+
+
+def test_batch_packing_cutoff_and_split_modes(pf3, oracle):
+    """Every packing cutoff 0..16 and every split mode (fixed, automatic at
+    1..32 items per warp) gives the oracle's results on a mixed batch whose
+    small sizes straddle the cutoffs and whose large ones get split."""
+    keep = pf3.get_batch_tuning()
+    rng = np.random.default_rng(41)
+    ns = [int(x) for x in rng.integers(0, 17, size=300)] + [16] * 40 + [11] * 33 + [20, 23, 26, 29, 33, 35]
+    mats = [inputs.uniform_matrix(9400 + k, n) for k, n in enumerate(ns)]
+    want = [oracle.perm_mod3(M) if M.shape[0] <= 24 else None for M in mats]
+    for k, M in enumerate(mats):
+        if want[k] is None:
+            want[k] = pf3.perm_f3(M)
+    try:
+        for tiny in range(0, 17):
+            pf3.set_batch_tuning(tiny, 28, 0, 8)
+            assert list(pf3.perm_f3_batch(mats)) == want, tiny
+        for mode in ((28, 22), (20, 20), (0, 0)):
+            for g in (1, 4, 32):
+                pf3.set_batch_tuning(10, mode[0], mode[1], g)
+                assert list(pf3.perm_f3_batch(mats)) == want, (mode, g)
+    finally:
+        pf3.set_batch_tuning(*keep.values())
 
 
 def test_autotune_keeps_results(pf3, oracle):
     rep = pf3.autotune()
     assert all(t > 0 for t in rep["single_ms"][1] + rep["single_ms"][2])
+    bt = rep["batch_tuning"]
+    U = pf3.variant_info(pf3.BATCH, rep["batch_variant"][1])["U"]
+    assert min(U, 16) <= bt["tiny_cutoff"] <= 16 and bt["chunk_log2"] == 0
+    assert bt["items_per_warp"] in (1, 2, 4, 8, 16) and all(t > 0 for t in rep["split_ms"].values())
+    # the cutoff is the last n (counting up) at which the packed walk won
+    for n, (packed, warp) in rep["pack_ms"].items():
+        assert (packed < warp) == (n <= bt["tiny_cutoff"]), (n, packed, warp, bt)
     A = inputs.uniform_matrix(8300, 21)
     assert pf3.perm_f3_counts(A) == oracle.counts(T(A))
 
@@ -372,12 +404,16 @@ def test_autotune_cache_roundtrip(tmp_path):
     code = ("import sys; sys.path.insert(0, %r)\n"
             "from paper_2407_20205_gb300 import binding as b\n"
             "r = b.autotune()\n"
-            "print(r['single_variant'][1], r['single_variant'][2], r['batch_variant'][1], r['batch_variant'][2])\n") % root
+            "t = r['batch_tuning']\n"
+            "print(r['single_variant'][1], r['single_variant'][2], r['batch_variant'][1], r['batch_variant'][2],"
+            " t['tiny_cutoff'], t['items_per_warp'])\n") % root
     first = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
     line = cache.read_text().strip().splitlines()[-1]
-    assert line.split("|")[-4:] == first.stdout.split()
+    assert line.split("|")[-6:] == first.stdout.split()
     code2 = ("import sys; sys.path.insert(0, %r)\n"
              "from paper_2407_20205_gb300 import binding as b\n"
-             "print(b.get_variant(0, 1), b.get_variant(0, 2), b.get_variant(1, 1), b.get_variant(1, 2))\n") % root
+             "t = b.get_batch_tuning()\n"
+             "print(b.get_variant(0, 1), b.get_variant(0, 2), b.get_variant(1, 1), b.get_variant(1, 2),"
+             " t['tiny_cutoff'], t['items_per_warp'])\n") % root
     second = subprocess.run([sys.executable, "-c", code2], env=env, capture_output=True, text=True, check=True)
     assert second.stdout.split() == first.stdout.split()
