@@ -379,7 +379,9 @@ def run_ours(args):
                            "results": {str(n): results[n] for n in SIZES},
                            "ms_per_launch": {str(n): float(np.mean(v)) for n, v in launch_ms.items()},
                            "parallelism": f"range split x{world}" if world > 1 else "1 GPU",
-                           "variants": {"single": tune["single_variant"], "batch": tune["batch_variant"]},
+                           "variants": {"single": tune["single_variant"],
+                                        "single_short_launches": tune["single_short_variant"],
+                                        "batch": tune["batch_variant"]},
                            "batch_tuning": tune["batch_tuning"],
                            "autotune_ms": {"single": tune["single_ms"], "batch": tune["batch_ms"],
                                            "pack_packed_vs_warp": {str(n): v for n, v in tune["pack_ms"].items()},

@@ -258,9 +258,14 @@ int pf3_device_info(int* sm_count, int* device);
 
 /* ------------------------------------------------------------ tuning */
 
-/* Kernel variants (probe group and unrolled block lengths, register budget).  which: 0 =
- * single-matrix kernel, 1 = batch kernel.  W: words per plane (1 for n <= 32,
- * 2 for n <= 64).  Results never depend on the variant, only speed does. */
+/* Kernel variants (probe group and unrolled block lengths, register budget,
+ * CTA size).  which: 0 = single-matrix kernel, 1 = batch kernel, 2 =
+ * single-matrix kernel for launches of fewer than 2^28 Gray indices (their
+ * own size class: there the fixed costs of a launch decide).  W: words per
+ * plane (1 for n <= 32, 2 for n <= 64).  pf3_set_variant(0, W, v) sets both
+ * single-matrix classes; (2, W, v) only the short one; pf3_get_variant(0, W)
+ * reads the long class.  Results never depend on the variant, only speed
+ * does. */
 int pf3_variant_count(int which);
 int pf3_set_variant(int which, int W, int v);
 int pf3_get_variant(int which, int W);
@@ -331,8 +336,13 @@ int pf3_batch_plan(const int32_t* ns, int64_t count, int tiny_cutoff, int split_
                    int items_per_warp, const int* variant, const int* warps, pf3_plan_item* items, int64_t capacity,
                    int64_t* num_items, int* auto_chunk_log2);
 
-/* Time every variant on the current device and keep the fastest per W, then
- * pick the batch packing cutoff and split granularity (pf3_autotune_ex).
+/* Time every variant on the current device and keep the fastest per W (a
+ * variant replaces the current choice, variant 0 first, only when it is at
+ * least 1 % faster) (single-matrix kernel: n = 32 over 2^31 Gray indices for W = 1, n = 40 over
+ * 2^36 for W = 2, and for the short-launch class n = 24 over 2^24 and n = 36
+ * over 2^27; batch kernel: 8192 matrices of n = 24 and 32 of n = 33 under the
+ * guided split), then pick the batch packing cutoff and split granularity
+ * (pf3_autotune_ex).
  * single_ms (pf3_variant_count(0) * 2 doubles) and batch_ms
  * (pf3_variant_count(1) * 2 doubles) receive the variant timings, W = 1
  * first; either may be NULL.  Takes a few seconds.  When the environment
@@ -341,7 +351,9 @@ int pf3_batch_plan(const int32_t* ns, int64_t count, int tiny_cutoff, int split_
  * the device. */
 int pf3_autotune(double* single_ms, double* batch_ms);
 
-/* pf3_autotune with the timings of its batch planning stages:
+/* pf3_autotune with the timings of all its stages.  single_short_ms
+ * (pf3_variant_count(2) * 2 doubles, may be NULL): the short-launch class, per
+ * variant, W = 1 first.  The batch planning stages:
  * pack_ms (2 * (PF3_TINY_MAX_N + 1) doubles, may be NULL): [n] the packed
  * walk and [PF3_TINY_MAX_N + 1 + n] the warp walk of a full grid of n x n
  * matrices, for n from the W = 1 batch variant's U + 1 up to the first n at
@@ -352,7 +364,8 @@ int pf3_autotune(double* single_ms, double* batch_ms);
  * the guided split with items_per_warp 1, 2, 4, 8, 16; the fastest total is
  * kept, ties within 1 % going to fewer items.  Takes a few seconds. */
 #define PF3_SPLIT_CANDIDATES 5
-int pf3_autotune_ex(double* single_ms, double* batch_ms, double* pack_ms, double* split_ms);
+int pf3_autotune_ex(double* single_ms, double* single_short_ms, double* batch_ms, double* pack_ms,
+                    double* split_ms);
 
 #ifdef __cplusplus
 }

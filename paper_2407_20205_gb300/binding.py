@@ -79,7 +79,7 @@ _lib_vinfo = _sig("pf3_variant_info", ctypes.c_int, [ctypes.c_int, ctypes.c_int,
 _lib_split = _sig("pf3_set_batch_split", ctypes.c_int, [ctypes.c_int, ctypes.c_int])
 _lib_vthreads = _sig("pf3_variant_threads", ctypes.c_int, [ctypes.c_int, ctypes.c_int])
 _lib_autotune = _sig("pf3_autotune", ctypes.c_int, [_dp, _dp])
-_lib_autotune_ex = _sig("pf3_autotune_ex", ctypes.c_int, [_dp, _dp, _dp, _dp])
+_lib_autotune_ex = _sig("pf3_autotune_ex", ctypes.c_int, [_dp, _dp, _dp, _dp, _dp])
 _lib_set_btune = _sig("pf3_set_batch_tuning", ctypes.c_int, [ctypes.c_int] * 4)
 _lib_get_btune = _sig("pf3_get_batch_tuning", ctypes.c_int, [_ip] * 4)
 
@@ -432,7 +432,7 @@ def device_info() -> dict:
 
 # ------------------------------------------------------------ tuning
 
-SINGLE, BATCH = 0, 1
+SINGLE, BATCH, SINGLE_SHORT = 0, 1, 2
 
 
 def variant_count(which: int) -> int:
@@ -500,12 +500,16 @@ def autotune() -> dict:
     cutoff), the split-granularity timings, and the choices made."""
     ns, nb = variant_count(SINGLE), variant_count(BATCH)
     a = (ctypes.c_double * (2 * ns))()
+    a2 = (ctypes.c_double * (2 * ns))()
     b = (ctypes.c_double * (2 * nb))()
     pk = (ctypes.c_double * (2 * (TINY_MAX_N + 1)))()
     sp = (ctypes.c_double * len(SPLIT_CANDIDATES))()
-    _check(_lib_autotune_ex(a, b, pk, sp), "pf3_autotune_ex")
+    _check(_lib_autotune_ex(a, a2, b, pk, sp), "pf3_autotune_ex")
     pk = list(pk)
-    return {"single_ms": {1: list(a)[:ns], 2: list(a)[ns:]}, "batch_ms": {1: list(b)[:nb], 2: list(b)[nb:]},
+    return {"single_ms": {1: list(a)[:ns], 2: list(a)[ns:]},
+            "single_short_ms": {1: list(a2)[:ns], 2: list(a2)[ns:]},
+            "single_short_variant": {W: get_variant(SINGLE_SHORT, W) for W in (1, 2)},
+            "batch_ms": {1: list(b)[:nb], 2: list(b)[nb:]},
             "pack_ms": {n: [pk[n], pk[TINY_MAX_N + 1 + n]] for n in range(TINY_MAX_N + 1) if pk[n] > 0},
             "split_ms": dict(zip(SPLIT_CANDIDATES, list(sp))),
             "single_variant": {W: get_variant(SINGLE, W) for W in (1, 2)},

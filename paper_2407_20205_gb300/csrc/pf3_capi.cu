@@ -98,7 +98,8 @@ int enqueue_range(DeviceCtx* c, const uint8_t* dA, int n, uint64_t first, uint64
                   cudaStream_t stream)
 {
     const int W = n <= 32 ? 1 : 2;
-    const int v = c->single_variant[W - 1];
+    const bool is_short = last - first < kShortLaunch - 1;
+    const int v = is_short ? c->single_variant_short[W - 1] : c->single_variant[W - 1];
     SingleArgs a;
     std::memset(&a, 0, sizeof(a));
     plan_range(n, first, last, kSingleVariants[v].U, a);

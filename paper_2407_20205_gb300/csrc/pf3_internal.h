@@ -17,10 +17,13 @@ struct KernelVariant {
     int threads;
 };
 constexpr int kMaxVariants = 16;
-constexpr int kNumSingleVariants = 8;
-constexpr KernelVariant kSingleVariants[kNumSingleVariants] = {{9, 5, 2, 256}, {9, 4, 2, 256}, {8, 4, 2, 256},
-                                                               {10, 5, 2, 256}, {8, 5, 2, 256}, {9, 5, 3, 256},
-                                                               {9, 5, 1, 256}, {9, 5, 4, 128}};
+// Single-matrix launches of fewer Gray indices than this form their own size
+// class for variant selection (their fixed costs decide, not the walk's rate).
+constexpr uint64_t kShortLaunch = 1ull << 28;
+constexpr int kNumSingleVariants = 9;
+constexpr KernelVariant kSingleVariants[kNumSingleVariants] = {
+    {9, 5, 2, 256}, {9, 4, 2, 256}, {8, 4, 2, 256}, {10, 5, 2, 256}, {8, 5, 2, 256},
+    {9, 5, 3, 256}, {9, 5, 1, 256}, {9, 5, 4, 128}, {9, 6, 1, 384}};
 constexpr int kNumBatchVariants = 6;
 constexpr KernelVariant kBatchVariants[kNumBatchVariants] = {{9, 5, 4, 128}, {9, 4, 4, 128}, {8, 4, 4, 128},
                                                              {9, 5, 2, 128}, {10, 5, 2, 128}, {8, 5, 4, 128}};

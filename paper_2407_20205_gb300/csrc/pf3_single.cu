@@ -206,8 +206,10 @@ const void* single_kernel_ptr(int v)
                                                    kSingleVariants[5].threads>;
     case 6: return (const void*)single_kernel<W, kSingleVariants[6].U, kSingleVariants[6].G, kSingleVariants[6].min_ctas,
                                                    kSingleVariants[6].threads>;
-    default: return (const void*)single_kernel<W, kSingleVariants[7].U, kSingleVariants[7].G, kSingleVariants[7].min_ctas,
+    case 7: return (const void*)single_kernel<W, kSingleVariants[7].U, kSingleVariants[7].G, kSingleVariants[7].min_ctas,
                                                    kSingleVariants[7].threads>;
+    default: return (const void*)single_kernel<W, kSingleVariants[8].U, kSingleVariants[8].G, kSingleVariants[8].min_ctas,
+                                                   kSingleVariants[8].threads>;
     }
 }
 

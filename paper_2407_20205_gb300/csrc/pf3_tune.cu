@@ -59,6 +59,10 @@ void fill_uniform(uint8_t* out, size_t bytes, uint64_t seed)
 }
 
 constexpr int kSplitCandidates = PF3_SPLIT_CANDIDATES;  // items per warp 1, 2, 4, 8, 16
+// Another variant replaces the default (variant 0) only when it is at least
+// 1 % faster: below that the timings are noise, and a stable choice keeps
+// profiles and benchmarks of the default kernel meaningful.
+constexpr float kVariantMargin = 0.99f;
 static_assert(kTinyMaxN == PF3_TINY_MAX_N, "packing capacity");
 
 // average milliseconds of `reps` launches of fn after one warm-up
@@ -85,8 +89,8 @@ float time_ms(cudaStream_t s, int reps, F fn)
 // Autotune cache: a text file named by the environment variable
 // PF3_TUNE_CACHE, one line per GPU model:
 //   <device name>|<SM count>|<single W=1>|<single W=2>|<batch W=1>|<batch W=2>|
-//   <packing cutoff>|<split items per warp>
-// (lines without the last two fields set only the variants).
+//   <packing cutoff>|<split items per warp>|<short single W=1>|<short single W=2>
+// (shorter lines from earlier versions set only the fields they hold).
 static std::string tune_key(int device)
 {
     cudaDeviceProp prop;
@@ -108,22 +112,27 @@ void load_tune_cache(DeviceCtx* c)
     while (std::fgets(line, sizeof(line), f)) {
         std::string l(line);
         if (l.compare(0, key.size(), key) != 0 || l.size() <= key.size() || l[key.size()] != '|') continue;
-        int v[6];
-        const int got = std::sscanf(l.c_str() + key.size() + 1, "%d|%d|%d|%d|%d|%d", &v[0], &v[1], &v[2], &v[3],
-                                    &v[4], &v[5]);
-        if (got != 4 && got != 6) continue;
+        int v[8];
+        const int got = std::sscanf(l.c_str() + key.size() + 1, "%d|%d|%d|%d|%d|%d|%d|%d", &v[0], &v[1], &v[2],
+                                    &v[3], &v[4], &v[5], &v[6], &v[7]);
+        if (got != 4 && got != 6 && got != 8) continue;
         if (v[0] < 0 || v[0] >= kNumSingleVariants || v[1] < 0 || v[1] >= kNumSingleVariants || v[2] < 0 ||
             v[2] >= kNumBatchVariants || v[3] < 0 || v[3] >= kNumBatchVariants)
             continue;
-        if (got == 6 && (v[4] < 0 || v[4] > kTinyMaxN || v[5] < 1 || v[5] > 1024)) continue;
+        if (got >= 6 && (v[4] < 0 || v[4] > kTinyMaxN || v[5] < 1 || v[5] > 1024)) continue;
+        if (got == 8 && (v[6] < 0 || v[6] >= kNumSingleVariants || v[7] < 0 || v[7] >= kNumSingleVariants)) continue;
         c->single_variant[0] = v[0];
         c->single_variant[1] = v[1];
         c->tune.variant[0] = v[2];
         c->tune.variant[1] = v[3];
-        if (got == 6) {
+        if (got >= 6) {
             c->tune.tiny_cutoff = v[4];
             c->tune.items_per_warp = v[5];
             c->tune.chunk_log2 = 0;
+        }
+        if (got == 8) {
+            c->single_variant_short[0] = v[6];
+            c->single_variant_short[1] = v[7];
         }
     }
     std::fclose(f);
@@ -147,8 +156,9 @@ static void store_tune_cache(DeviceCtx* c)
     FILE* f = std::fopen(tmp.c_str(), "w");
     if (!f) return;
     for (const auto& l : keep) std::fputs(l.c_str(), f);
-    std::fprintf(f, "%s|%d|%d|%d|%d|%d|%d\n", key.c_str(), c->single_variant[0], c->single_variant[1],
-                 c->tune.variant[0], c->tune.variant[1], c->tune.tiny_cutoff, c->tune.items_per_warp);
+    std::fprintf(f, "%s|%d|%d|%d|%d|%d|%d|%d|%d\n", key.c_str(), c->single_variant[0], c->single_variant[1],
+                 c->tune.variant[0], c->tune.variant[1], c->tune.tiny_cutoff, c->tune.items_per_warp,
+                 c->single_variant_short[0], c->single_variant_short[1]);
     std::fclose(f);
     std::rename(tmp.c_str(), path);
 }
@@ -161,22 +171,21 @@ extern "C" {
 
 int pf3_variant_count(int which)
 {
-    if (which == 0) return kNumSingleVariants;
+    if (which == 0 || which == 2) return kNumSingleVariants;
     if (which == 1) return kNumBatchVariants;
     return PF3_EINVAL;
 }
 
 int pf3_set_variant(int which, int W, int v)
 {
-    if (W < 1 || W > 2 || v < 0) return PF3_EINVAL;
-    if ((which == 0 && v >= kNumSingleVariants) || (which == 1 && v >= kNumBatchVariants) || which < 0 ||
-        which > 1)
-        return PF3_EINVAL;
+    if (W < 1 || W > 2 || v < 0 || which < 0 || which > 2) return PF3_EINVAL;
+    if (v >= (which == 1 ? kNumBatchVariants : kNumSingleVariants)) return PF3_EINVAL;
     int rc;
     DeviceCtx* c = device_ctx(&rc);
     if (!c) return rc;
     std::lock_guard<std::mutex> g(c->mu);
-    if (which == 0) c->single_variant[W - 1] = v;
+    if (which == 0) c->single_variant[W - 1] = c->single_variant_short[W - 1] = v;
+    else if (which == 2) c->single_variant_short[W - 1] = v;
     else c->tune.variant[W - 1] = v;
     return PF3_OK;
 }
@@ -184,7 +193,7 @@ int pf3_set_variant(int which, int W, int v)
 int pf3_variant_info(int which, int v, int* U, int* G, int* min_ctas)
 {
     const KernelVariant* t = nullptr;
-    if (which == 0 && v >= 0 && v < kNumSingleVariants) t = &kSingleVariants[v];
+    if ((which == 0 || which == 2) && v >= 0 && v < kNumSingleVariants) t = &kSingleVariants[v];
     if (which == 1 && v >= 0 && v < kNumBatchVariants) t = &kBatchVariants[v];
     if (!t) return PF3_EINVAL;
     if (U) *U = t->U;
@@ -195,17 +204,18 @@ int pf3_variant_info(int which, int v, int* U, int* G, int* min_ctas)
 
 int pf3_variant_threads(int which, int v)
 {
-    if (which == 0 && v >= 0 && v < kNumSingleVariants) return kSingleVariants[v].threads;
+    if ((which == 0 || which == 2) && v >= 0 && v < kNumSingleVariants) return kSingleVariants[v].threads;
     if (which == 1 && v >= 0 && v < kNumBatchVariants) return kBatchVariants[v].threads;
     return PF3_EINVAL;
 }
 
 int pf3_get_variant(int which, int W)
 {
-    if (W < 1 || W > 2 || which < 0 || which > 1) return PF3_EINVAL;
+    if (W < 1 || W > 2 || which < 0 || which > 2) return PF3_EINVAL;
     int rc;
     DeviceCtx* c = device_ctx(&rc);
     if (!c) return rc;
+    if (which == 2) return c->single_variant_short[W - 1];
     return which == 0 ? c->single_variant[W - 1] : c->tune.variant[W - 1];
 }
 
@@ -251,16 +261,18 @@ int pf3_get_batch_tuning(int* tiny_cutoff, int* split_cutoff, int* chunk_log2, i
     return PF3_OK;
 }
 
-int pf3_autotune_ex(double* single_ms, double* batch_ms, double* pack_ms, double* split_ms)
+int pf3_autotune_ex(double* single_ms, double* single_short_ms, double* batch_ms, double* pack_ms,
+                    double* split_ms)
 {
     int rc;
     DeviceCtx* c = device_ctx(&rc);
     if (!c) return rc;
     std::lock_guard<std::mutex> g(c->mu);
     cudaStream_t s = c->stream;
-    // ---- single-matrix kernel: n = 32 over 2^31 indices, n = 40 over 2^34
+    // ---- single-matrix kernel: n = 32 over 2^31 indices (fixed shares), n =
+    // 40 over 2^36 (long enough for the guided chunks the benchmark sizes use)
     const int nW[2] = {32, 40};
-    const int lgW[2] = {31, 34};
+    const int lgW[2] = {31, 36};
     uint8_t* dA = nullptr;
     unsigned long long* dout = nullptr;
     cudaError_t e = cudaMalloc(&dA, kMaxNN);
@@ -282,18 +294,44 @@ int pf3_autotune_ex(double* single_ms, double* batch_ms, double* pack_ms, double
                 enqueue_range(c, dA, n, 0, (1ull << lgW[W - 1]) - 1, dout, s);
             });
             if (single_ms) single_ms[(W - 1) * kNumSingleVariants + v] = ms;
-            if (ms < best) {
+            if (v == 0 || ms < kVariantMargin * best) {
                 best = ms;
                 bestv = v;
             }
         }
         c->single_variant[W - 1] = bestv;
     }
-    // ---- batch kernel variants: 3072 whole matrices of n = 24 (W = 1); 20
-    // matrices of n = 33 cut into split items (W = 2)
+    // ---- short single-matrix launches (under kShortLaunch indices), where
+    // the fixed costs of a launch decide: n = 24 over all 2^24 indices (W = 1)
+    // and n = 36 over 2^27 (W = 2), 20 launches per variant
+    const int nS[2] = {24, 36};
+    const int lgS[2] = {24, 27};
+    for (int W = 1; W <= 2; ++W) {
+        const int n = nS[W - 1];
+        sample_matrix(hA.data(), n, 2000 + n);
+        cudaMemcpy(dA, hA.data(), (size_t)n * n, cudaMemcpyHostToDevice);
+        float best = 1e30f;
+        int bestv = 0;
+        for (int v = 0; v < kNumSingleVariants; ++v) {
+            c->single_variant_short[W - 1] = v;
+            const float ms = time_ms(s, 20, [&] {
+                enqueue_range(c, dA, n, 0, (1ull << lgS[W - 1]) - 1, dout, s);
+            });
+            if (single_short_ms) single_short_ms[(W - 1) * kNumSingleVariants + v] = ms;
+            if (v == 0 || ms < kVariantMargin * best) {
+                best = ms;
+                bestv = v;
+            }
+        }
+        c->single_variant_short[W - 1] = bestv;
+    }
+    // ---- batch kernel variants, each under the guided split: 8192 matrices
+    // of n = 24 (W = 1) and 32 of n = 33 (W = 2), a few grids' worth of work,
+    // so that the variants are compared on throughput, not on how their
+    // warp counts happen to fit the last round
     int warps[2];
     const int bn[2] = {24, 33};
-    const int bcount[2] = {3072, 20};
+    const int bcount[2] = {8192, 32};
     for (int W = 1; W <= 2 && e == cudaSuccess; ++W) {
         const int n = bn[W - 1], cnt = bcount[W - 1];
         std::vector<int32_t> ns(cnt, n);
@@ -309,8 +347,7 @@ int pf3_autotune_ex(double* single_ms, double* batch_ms, double* pack_ms, double
         }
         cudaMemcpy(dAs, hAs.data(), hAs.size(), cudaMemcpyHostToDevice);
         const BatchTuning keep = c->tune;
-        c->tune.chunk_log2 = 26;
-        c->tune.cutoff = (W == 1) ? PF3_MAX_N : 28;  // W = 1: whole matrices per warp
+        c->tune.chunk_log2 = 0;
         float best = 1e30f;
         int bestv = 0;
         for (int v = 0; v < kNumBatchVariants; ++v) {
@@ -320,7 +357,7 @@ int pf3_autotune_ex(double* single_ms, double* batch_ms, double* pack_ms, double
             plan_batch(ns.data(), cnt, c->tune, warps, plan);
             const float ms = time_ms(s, 1, [&] { enqueue_batch(c, plan, dAs, dres, nullptr, s); });
             if (batch_ms) batch_ms[(W - 1) * kNumBatchVariants + v] = ms;
-            if (ms < best) {
+            if (v == 0 || ms < kVariantMargin * best) {
                 best = ms;
                 bestv = v;
             }
@@ -434,6 +471,9 @@ int pf3_autotune_ex(double* single_ms, double* batch_ms, double* pack_ms, double
     return cuda_rc(e);
 }
 
-int pf3_autotune(double* single_ms, double* batch_ms) { return pf3_autotune_ex(single_ms, batch_ms, nullptr, nullptr); }
+int pf3_autotune(double* single_ms, double* batch_ms)
+{
+    return pf3_autotune_ex(single_ms, nullptr, batch_ms, nullptr, nullptr);
+}
 
 }  // extern "C"

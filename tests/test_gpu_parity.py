@@ -139,6 +139,34 @@ def test_range_partition_adds_up(pf3):
         assert tuple(tot) == whole
 
 
+def test_guided_chunks_match_fixed_shares(pf3):
+    """A launch of at least 512 Gray blocks per lane hands its blocks out in
+    guided chunks from an atomic cursor; shorter ones give each thread a
+    fixed share.  A range just above that size (ragged ends included) must
+    count the same as its pieces below it, walked with fixed shares, and
+    the whole-matrix walk of a 36 x 36 matrix (guided) must equal the sum of
+    its eight 2^33 eighths (fixed shares)."""
+    info = pf3.device_info()
+    ctas = 2 * info["sm_count"]  # the default W = 2 variant: 2 CTAs of 256 threads per SM
+    per_lane = 512 * 512  # blocks of 2^9 indices
+    threshold = ctas * 256 * per_lane
+    A = inputs.uniform_matrix(4100, 40)
+    a = 98765
+    b = a + threshold + 3 * (1 << 20) + 777
+    whole = pf3.perm_f3_range_counts(A, a, b)
+    cuts = [a, a + threshold // 3, a + 2 * (threshold // 3), b + 1]
+    tot = [0, 0]
+    for lo, hi in zip(cuts[:-1], cuts[1:]):
+        p, m = pf3.perm_f3_range_counts(A, lo, hi - 1)
+        tot[0] += p
+        tot[1] += m
+    assert tuple(tot) == whole
+    B = inputs.uniform_matrix(4101, 36)
+    eighth = 1 << 33
+    parts = [pf3.perm_f3_range_counts(B, k * eighth, (k + 1) * eighth - 1) for k in range(8)]
+    assert (sum(p for p, _ in parts), sum(m for _, m in parts)) == pf3.perm_f3_counts(B)
+
+
 # known answers at the benchmark sizes (n = 36, 40): closed forms and
 # oracle-sized factors; every one walks all 2^n Gray indices on the GPU
 
@@ -406,14 +434,15 @@ def test_autotune_cache_roundtrip(tmp_path):
             "r = b.autotune()\n"
             "t = r['batch_tuning']\n"
             "print(r['single_variant'][1], r['single_variant'][2], r['batch_variant'][1], r['batch_variant'][2],"
-            " t['tiny_cutoff'], t['items_per_warp'])\n") % root
+            " t['tiny_cutoff'], t['items_per_warp'], r['single_short_variant'][1], r['single_short_variant'][2])\n"
+            ) % root
     first = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
     line = cache.read_text().strip().splitlines()[-1]
-    assert line.split("|")[-6:] == first.stdout.split()
+    assert line.split("|")[-8:] == first.stdout.split()
     code2 = ("import sys; sys.path.insert(0, %r)\n"
              "from paper_2407_20205_gb300 import binding as b\n"
              "t = b.get_batch_tuning()\n"
              "print(b.get_variant(0, 1), b.get_variant(0, 2), b.get_variant(1, 1), b.get_variant(1, 2),"
-             " t['tiny_cutoff'], t['items_per_warp'])\n") % root
+             " t['tiny_cutoff'], t['items_per_warp'], b.get_variant(2, 1), b.get_variant(2, 2))\n") % root
     second = subprocess.run([sys.executable, "-c", code2], env=env, capture_output=True, text=True, check=True)
     assert second.stdout.split() == first.stdout.split()

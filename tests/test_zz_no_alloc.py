@@ -73,3 +73,21 @@ def test_noalloc_limits_and_bad_entries(env):
     pf3.perm_f3_range_counts_noalloc(dA, 20, 0, (1 << 20) - 1, out, 0, s)
     s.synchronize()
     assert out.cpu().tolist() == ref.cpu().tolist()
+
+
+def test_noalloc_small_grids_take_every_chunk_phase(env):
+    """With 1, 3 or 7 CTAs a 2^31-index range is far above 512 blocks per
+    lane, so the few warps run every guided phase and the tail chunks; the
+    counts must equal the allocating entry point's (full grid)."""
+    torch, pf3 = env
+    s = torch.cuda.Stream()
+    A = inputs.uniform_matrix(914, 36)
+    dA = torch.from_numpy(A).cuda()
+    ref = torch.zeros(3, dtype=torch.int64, device="cuda")
+    first, last = 4321, (1 << 31) + 98765
+    pf3.perm_f3_range_counts_async(dA, 36, first, last, ref, s)
+    for ctas in (1, 3, 7):
+        out = torch.full((3,), 7, dtype=torch.int64, device="cuda")
+        pf3.perm_f3_range_counts_noalloc(dA, 36, first, last, out, ctas, s)
+        s.synchronize()
+        assert out.cpu().tolist() == ref.cpu().tolist(), ctas
