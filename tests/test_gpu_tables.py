@@ -74,3 +74,14 @@ def test_config3_full_batch_sampled_and_histogram(pf3, oracle):
     sd = math.sqrt(count * (1 / 3) * (2 / 3))
     assert abs(h[0] - count / 3) < 4 * sd
     assert abs(h[1] - h[2]) < 4 * math.sqrt(2 * count / 3)
+    # every one of the 200,000 results against the single-matrix kernel (its
+    # own launch per matrix, fixed per-thread shares; itself checked against
+    # the oracle in test_gpu_parity.py): catches planning, packing and
+    # guided-split mistakes of the batch path at full size
+    single = torch.zeros((count, 3), dtype=torch.int64, device="cuda")
+    dA = dAs.view(count, n * n)
+    last = (1 << n) - 1
+    for k in range(count):
+        pf3.perm_f3_range_counts_async(dA[k], n, 0, last, single[k], s)
+    s.synchronize()
+    assert single[:, 2].cpu().numpy().astype(np.uint8).tolist() == r.tolist()
