@@ -80,12 +80,12 @@ template <int W, int U, int G, int MINB>
 __global__ void __launch_bounds__(kBatchThreads, MINB) batch_kernel(BatchArgs a)
 {
     __shared__ RowTable<W> tabs[kBatchThreads / 32];
-    __shared__ WarpQueue queues[kBatchThreads / 32];
+    __shared__ WarpQueue<G> queues[kBatchThreads / 32];
     __shared__ TinyTable tiny[W == 1 ? kBatchThreads / 32 : 1];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     RowTable<W>& tab = tabs[warp];
-    WarpQueue& q = queues[warp];
+    WarpQueue<G>& q = queues[warp];
     if (lane == 0) q.count = 0;
     __syncwarp();
 
@@ -143,7 +143,8 @@ __global__ void __launch_bounds__(kBatchThreads, MINB) batch_kernel(BatchArgs a)
                 uint64_t s, len;
                 split_range(it.NB, 32, (uint64_t)lane, s, len);
                 const uint64_t trip = __shfl_sync(0xFFFFFFFFu, len, 0);
-                walk_groups<W, G, U>(tab, R, n, it.B0 + s, len, trip, q, lane, c);
+                const uint64_t done = walk_groups<W, G, U>(tab, R, n, it.B0 + s, len, trip, q, lane, c);
+                if (done < len) walk_dense<W, G, U>(tab, q.dk, n, it.B0 + s + done, len - done, &c);
             }
         }
         const unsigned long long p = warp_sum(c.plus);

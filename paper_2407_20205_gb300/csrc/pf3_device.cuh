@@ -316,24 +316,37 @@ __device__ __noinline__ void replay_group(const RowTable<W>& tab, int n, uint64_
 // Lanes push as they find marks; the whole warp drains the queue together,
 // one group per lane, so a rare replay does not stall 31 idle lanes.
 constexpr int kQueueCap = 64;
+// Queued marks at a block's end at which a warp leaves the low-word walk for
+// the dense walk: at least 129 of the block's 32 x 2^(U-G) groups marked
+// (a quarter for U - G = 4), where replaying them one by one costs more.
+constexpr unsigned kDenseSwitch = 160;
 
+// A warp's queue slot.  Once a warp switches to the dense walk its queue is
+// empty, so the same bytes hold the dense walk's subset masks: for each
+// nonzero subset s of rows 0..G-1, (K1, K2) of word 0 and (K1, K2) of word 1
+// of the constant sum_{r in s} row_r.
+template <int G>
 struct WarpQueue {
+    union {
+        unsigned long long i0[kQueueCap];
+        uint4 dk[(1 << G) - 1];
+    };
     unsigned count;
     unsigned pad;
-    unsigned long long i0[kQueueCap];
 };
 
 template <int W, int G>
-__device__ __noinline__ void queue_push(WarpQueue& q, const RowTable<W>& tab, int n, uint64_t i0, Counts* c)
+__device__ __noinline__ void queue_push(WarpQueue<G>& q, const RowTable<W>& tab, int n, uint64_t i0, Counts* c)
 {
     const unsigned slot = atomicAdd(&q.count, 1u);
     if (slot < (unsigned)kQueueCap) q.i0[slot] = i0;
     else replay_group<W, G>(tab, n, i0, *c);  // queue full: replay in place
 }
 
-// all 32 lanes: replay the queued groups and empty the queue
+// all 32 lanes: replay the queued groups and empty the queue (out of line:
+// it is rare, and kept inline it took instruction-cache room from the walk)
 template <int W, int G>
-__device__ __forceinline__ void queue_drain(WarpQueue& q, const RowTable<W>& tab, int n, int lane, Counts& c)
+__device__ __noinline__ void queue_drain(WarpQueue<G>& q, const RowTable<W>& tab, int n, int lane, Counts& c)
 {
     __syncwarp();
     const unsigned cnt = *(volatile unsigned*)&q.count;
@@ -345,10 +358,73 @@ __device__ __forceinline__ void queue_drain(WarpQueue& q, const RowTable<W>& tab
     __syncwarp();
 }
 
+// all 32 lanes: the dense walk's subset masks into the warp's queue slot
+template <int W, int G>
+__device__ __noinline__ void build_dense_masks(WarpQueue<G>& q, const RowTable<W>& tab, int lane)
+{
+    for (int j = lane; j < (1 << G) - 1; j += 32) {
+        uint32_t k1[W], k2[W];
+        subset_masks<W>(tab, (uint64_t)(j + 1), k1, k2);
+        q.dk[j] = make_uint4(k1[0], k2[0], W > 1 ? k1[W - 1] : 0u, W > 1 ? k2[W - 1] : 0u);
+    }
+    __syncwarp();
+}
+
+// Exact walk of Gray blocks [B0, B0 + len) for matrices whose terms are often
+// nonzero (the low-word test would mark most groups, and replaying them one
+// by one costs far more): group K's 2^G states are its base state plus each
+// subset s of rows 0..G-1, every one evaluated in full (all words) from the
+// base and the subset masks, with the exact sign.  The base of an even group
+// is its first index and of an odd group its last, so |S| is even exactly
+// for even K, and consecutive bases differ in row G + tz(K+1), subtracted
+// iff bit tz(K+1)+1 of K+1 is set (the Gray flip at index (K+1)·2^G).
+template <int W, int G, int U>
+__device__ __noinline__ void walk_dense(const RowTable<W>& tab, const uint4* dk, int n, uint64_t B0, uint64_t len,
+                                        Counts* c)
+{
+    if (!len) return;
+    State<W> base = seed_state<W>(tab, n, B0 << U);
+    const uint64_t K_end = (B0 + len) << (U - G);
+    unsigned long long plus = 0, minus = 0;
+    for (uint64_t K = B0 << (U - G);;) {
+        const uint32_t kpar = (uint32_t)K & 1u;
+        if (all_ones<W>(base)) {
+            uint32_t par = kpar;
+#pragma unroll
+            for (int w = 0; w < W; ++w) par += __popc(base.s[w]);
+            if (par & 1u) ++minus;
+            else ++plus;
+        }
+#pragma unroll 7
+        for (int sub = 1; sub < (1 << G); ++sub) {
+            const uint4 k = dk[sub - 1];
+            uint32_t m0 = base.m[0], s0 = base.s[0];
+            add_word(m0, s0, k.x, k.y);
+            bool nz = (m0 == 0xFFFFFFFFu);
+            uint32_t par = kpar + (uint32_t)__popc((unsigned)sub) + (uint32_t)__popc(s0);
+            if (W > 1) {
+                uint32_t m1 = base.m[W - 1], s1 = base.s[W - 1];
+                add_word(m1, s1, k.z, k.w);
+                nz = nz && (m1 == 0xFFFFFFFFu);
+                par += (uint32_t)__popc(s1);
+            }
+            if (nz) {
+                if (par & 1u) ++minus;
+                else ++plus;
+            }
+        }
+        if (++K == K_end) break;
+        const int z = __ffsll((long long)K) - 1;
+        add_row<W>(base, tab, (int)((K >> (z + 1)) & 1u), G + z);
+    }
+    c->plus += plus;
+    c->minus += minus;
+}
+
 template <int W, int G, int U, int GI>
 struct GroupSteps {
     static __device__ __forceinline__ void run(uint32_t& m, uint32_t& sg, const GroupRows<G, U>& R, uint32_t kmid2,
-                                               uint64_t ibase, WarpQueue& q, const RowTable<W>& tab, int n,
+                                               uint64_t ibase, WarpQueue<G>& q, const RowTable<W>& tab, int n,
                                                Counts& c)
     {
         GroupSteps<W, G, U, GI - 1>::run(m, sg, R, kmid2, ibase, q, tab, n, c);
@@ -376,17 +452,21 @@ struct GroupSteps {
 template <int W, int G, int U>
 struct GroupSteps<W, G, U, 0> {
     static __device__ __forceinline__ void run(uint32_t&, uint32_t&, const GroupRows<G, U>&, uint32_t, uint64_t,
-                                               WarpQueue&, const RowTable<W>&, int, Counts&)
+                                               WarpQueue<G>&, const RowTable<W>&, int, Counts&)
     {
     }
 };
 
 // Walk blocks [B0, B0 + len) of 2^U indices.  `trip` (>= len) must be the
 // same in all 32 lanes of the warp: lanes with len < trip idle through the
-// extra iterations so that the warp drains its queue together.
+// extra iterations so that the warp drains its queue together.  Returns the
+// number of blocks walked; when it is below len the warp has switched to the
+// dense walk (its masks are in q.dk) and the caller walks the rest with
+// walk_dense.
 template <int W, int G, int U>
-__device__ __forceinline__ void walk_groups(const RowTable<W>& tab, const GroupRows<G, U>& R, int n, uint64_t B0,
-                                            uint64_t len, uint64_t trip, WarpQueue& q, int lane, Counts& c)
+__device__ __forceinline__ uint64_t walk_groups(const RowTable<W>& tab, const GroupRows<G, U>& R, int n,
+                                                uint64_t B0, uint64_t len, uint64_t trip, WarpQueue<G>& q, int lane,
+                                                Counts& c)
 {
     uint32_t m = 0, sg = 0;  // low word of the base state
     if (len) seed_low<W>(tab, n, B0 << U, m, sg);
@@ -406,9 +486,21 @@ __device__ __forceinline__ void walk_groups(const RowTable<W>& tab, const GroupR
             }
         }
         __syncwarp();
-        if (*(volatile unsigned*)&q.count >= 32u) queue_drain<W, G>(q, tab, n, lane, c);
+        const unsigned cnt = *(volatile unsigned*)&q.count;
+        if (__builtin_expect(cnt >= 32u, 0)) {
+            // the queue is drained whenever it holds 32 at a block's end, so
+            // a count of kDenseSwitch means that this block alone marked at
+            // least kDenseSwitch - 31 groups: finish the walked groups
+            // exactly, then walk the rest densely
+            queue_drain<W, G>(q, tab, n, lane, c);
+            if (cnt >= kDenseSwitch) {
+                build_dense_masks<W, G>(q, tab, lane);
+                return it + 1 < len ? it + 1 : len;
+            }
+        }
     }
     queue_drain<W, G>(q, tab, n, lane, c);
+    return len;
 }
 
 // balanced split of `total` items over `parts`: part k gets [start, start+len)

@@ -48,7 +48,7 @@ template <int W, int U, int G, int MINB, int THREADS>
 __global__ void __launch_bounds__(THREADS, MINB) single_kernel(SingleArgs a)
 {
     __shared__ RowTable<W> tab;
-    __shared__ WarpQueue queues[THREADS / 32];
+    __shared__ WarpQueue<G> queues[THREADS / 32];
     __shared__ unsigned long long red[2][THREADS / 32];
     __shared__ bool s_last;
 
@@ -70,7 +70,9 @@ __global__ void __launch_bounds__(THREADS, MINB) single_kernel(SingleArgs a)
                 uint64_t s, len;
                 split_range(a.mid_NB, T, tid, s, len);
                 const uint64_t trip = __shfl_sync(0xFFFFFFFFu, len, 0);  // lane 0 holds the longest share
-                walk_groups<W, G, U>(tab, R, a.n, a.mid_B0 + s, len, trip, queues[warp], lane, c);
+                const uint64_t done =
+                    walk_groups<W, G, U>(tab, R, a.n, a.mid_B0 + s, len, trip, queues[warp], lane, c);
+                if (done < len) walk_dense<W, G, U>(tab, queues[warp].dk, a.n, a.mid_B0 + s + done, len - done, &c);
             } else {
                 // the cursor only grows, and every chunk index at or past
                 // nchunks ends the loop: at most nchunks + 1 turns per warp
@@ -83,7 +85,10 @@ __global__ void __launch_bounds__(THREADS, MINB) single_kernel(SingleArgs a)
                     chunk_range(a, k, cs, clen);
                     split_range(clen, 32, (uint64_t)lane, s, len);
                     const uint64_t trip = __shfl_sync(0xFFFFFFFFu, len, 0);
-                    walk_groups<W, G, U>(tab, R, a.n, a.mid_B0 + cs + s, len, trip, queues[warp], lane, c);
+                    const uint64_t done =
+                        walk_groups<W, G, U>(tab, R, a.n, a.mid_B0 + cs + s, len, trip, queues[warp], lane, c);
+                    if (done < len)
+                        walk_dense<W, G, U>(tab, queues[warp].dk, a.n, a.mid_B0 + cs + s + done, len - done, &c);
                 }
             }
         }

@@ -10,7 +10,7 @@ import math
 import numpy as np
 import pytest
 
-from conftest import read_golden
+from conftest import rank_one_counts, read_golden
 from paper_2407_20205_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -165,6 +165,52 @@ def test_guided_chunks_match_fixed_shares(pf3):
     eighth = 1 << 33
     parts = [pf3.perm_f3_range_counts(B, k * eighth, (k + 1) * eighth - 1) for k in range(8)]
     assert (sum(p for p, _ in parts), sum(m for _, m in parts)) == pf3.perm_f3_counts(B)
+
+
+def _rank_one(seed, n):
+    rng = np.random.default_rng(seed)
+    d = rng.choice([1, -1], size=n)
+    e = rng.choice([1, -1], size=n)
+    A = np.outer(d, e) % 3
+    return A.astype(np.uint8), d, e
+
+
+@pytest.mark.parametrize("n", [14, 20, 27, 33, 36, 40])
+def test_dense_terms_closed_form(pf3, n):
+    """Matrices with 2/3 of their terms nonzero (all columns proportional)
+    send every warp into the dense walk: the exact counts must equal the
+    closed form, for J_n and for D1 J D2 with random signs."""
+    J = np.ones((n, n), np.uint8)
+    assert pf3.perm_f3_counts(J) == rank_one_counts([1] * n, [1] * n)
+    A, d, e = _rank_one(7000 + n, n)
+    assert pf3.perm_f3_counts(A) == rank_one_counts(list(d), list(e))
+
+
+def test_dense_terms_batch_and_ranges(pf3, oracle):
+    """The batch path on dense matrices (closed form), ranges that start and
+    end inside dense walks (additivity), and few-distinct-column matrices
+    where only some blocks switch, against the oracle."""
+    mats, want = [], []
+    for k, n in enumerate([14, 18, 22, 26, 30, 33, 35]):
+        A, d, e = _rank_one(7100 + k, n)
+        mats.append(A)
+        p, m = rank_one_counts(list(d), list(e))
+        want.append(((p - m) * (-1) ** n) % 3)
+    assert list(pf3.perm_f3_batch(mats)) == want
+    A, _, _ = _rank_one(7200, 34)
+    whole = pf3.perm_f3_range_counts(A, 12345, (1 << 33) + 777)
+    mid = (1 << 32) + 4321
+    lo = pf3.perm_f3_range_counts(A, 12345, mid - 1)
+    hi = pf3.perm_f3_range_counts(A, mid, (1 << 33) + 777)
+    assert (lo[0] + hi[0], lo[1] + hi[1]) == whole
+    rng = np.random.default_rng(7300)
+    for n in (16, 20, 23):
+        for pool in (2, 3):
+            cols = rng.integers(0, 3, size=(pool, n))
+            pick = rng.integers(0, pool, size=n)
+            scale = rng.choice([1, 2], size=n)
+            A = ((cols[pick].T * scale) % 3).astype(np.uint8)  # column j = scale_j * cols[pick_j]
+            assert pf3.perm_f3_counts(A) == oracle.counts(T(A)), (n, pool)
 
 
 # known answers at the benchmark sizes (n = 36, 40): closed forms and

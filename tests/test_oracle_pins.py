@@ -12,7 +12,7 @@ import math
 import numpy as np
 import pytest
 
-from conftest import read_golden
+from conftest import rank_one_counts, read_golden
 from paper_2407_20205_gb300 import inputs
 
 RNG_SEED = 20240729
@@ -143,6 +143,23 @@ def _direct_term(M, i):
     prod %= 3
     sign = -1 if len(cols) % 2 else 1
     return (sign * prod) % 3  # 0, 1 or 2 (2 == -1)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 11, 14])
+def test_rank_one_closed_form(oracle, n):
+    """A_ij = d_i e_j with d, e in {1, -1}: every row-subset sum is e_j times
+    t = sum_{i in S} d_i, so the exact +1/-1 term counts follow from
+    binomial coefficients (rank_one_counts).  Two thirds of these terms are
+    nonzero, unlike a random matrix's (2/3)^n.  The oracle walks column
+    subsets, so it is given A^T."""
+    rng = np.random.default_rng(900 + n)
+    for _ in range(3):
+        d = rng.choice([1, -1], size=n)
+        e = rng.choice([1, -1], size=n)
+        A = (np.outer(d, e) % 3).astype(np.uint8)
+        assert oracle.counts(np.ascontiguousarray(A.T)) == rank_one_counts(list(d), list(e))
+    J = np.ones((n, n), np.uint8)
+    assert oracle.counts(J) == rank_one_counts([1] * n, [1] * n)
 
 
 def test_range_single_index_terms(oracle):
