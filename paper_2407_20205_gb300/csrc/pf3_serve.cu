@@ -61,7 +61,6 @@ struct Job {
     uint64_t items_issued = 0;
     uint64_t t_submit = 0;
     uint64_t t_done = 0;
-    uint64_t remaining_work() const { return nb ? (nb - cursor) : (items_issued ? 0 : 1); }
 };
 
 struct Launch {
