@@ -336,6 +336,23 @@ int pf3_batch_plan(const int32_t* ns, int64_t count, int tiny_cutoff, int split_
                    int items_per_warp, const int* variant, const int* warps, pf3_plan_item* items, int64_t capacity,
                    int64_t* num_items, int* auto_chunk_log2);
 
+/* The single-matrix launch plan on the host alone (no device is touched):
+ * how Gray indices [first, last] of an n x n matrix are cut for variant
+ * `variant` of the single-matrix kernel on `grid` CTAs (Sec. 3.1's blocks of
+ * consecutive Gray states).  info (host, 12 uint64) receives: has_head,
+ * head_first, head_last (indices walked one by one before the first whole
+ * block), has_tail, tail_first, tail_last (after the last one), mid_B0,
+ * mid_NB (the whole blocks of 2^U indices in between), dynamic (1: warps take
+ * chunks of blocks from an atomic cursor; 0: each thread walks one contiguous
+ * share), U, threads per CTA, nchunks.  When dynamic, chunk_first/chunk_len
+ * (host, capacity entries each; both NULL to ask for the count only) receive
+ * each chunk's first block (relative to mid_B0) and length in blocks, in the
+ * order warps take them; *num_chunks receives their number (0 when not
+ * dynamic).  PF3_EINVAL on a bad argument, PF3_ETOOBIG when capacity is too
+ * small. */
+int pf3_range_plan(int n, uint64_t first, uint64_t last, int variant, int grid, uint64_t* info,
+                   uint64_t* chunk_first, uint64_t* chunk_len, int64_t capacity, int64_t* num_chunks);
+
 /* Time every variant on the current device and keep the fastest per W (a
  * variant replaces the current choice, variant 0 first, only when it is at
  * least 1 % faster) (single-matrix kernel: n = 32 over 2^31 Gray indices for W = 1, n = 40 over

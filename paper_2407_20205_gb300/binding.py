@@ -472,6 +472,30 @@ def get_batch_tuning() -> dict:
     return dict(zip(("tiny_cutoff", "split_cutoff", "chunk_log2", "items_per_warp"), (x.value for x in v)))
 
 
+_lib_range_plan = _sig("pf3_range_plan", ctypes.c_int,
+                       [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, _u64p, _u64p,
+                        _u64p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)])
+RANGE_PLAN_FIELDS = ("has_head", "head_first", "head_last", "has_tail", "tail_first", "tail_last", "mid_B0",
+                     "mid_NB", "dynamic", "U", "threads", "nchunks")
+
+
+def range_plan(n: int, first: int, last: int, variant: int = 0, grid: int = 304) -> dict:
+    """The single-matrix launch plan of Gray indices [first, last], computed on
+    the host (no device needed); chunks as (first block, blocks) relative to
+    mid_B0 when the launch hands out guided chunks."""
+    info = (ctypes.c_uint64 * 12)()
+    num = ctypes.c_int64()
+    _check(_lib_range_plan(n, first, last, variant, grid, info, None, None, 0, ctypes.byref(num)),
+           "pf3_range_plan")
+    cf = (ctypes.c_uint64 * max(1, num.value))()
+    cl = (ctypes.c_uint64 * max(1, num.value))()
+    _check(_lib_range_plan(n, first, last, variant, grid, info, cf, cl, num.value, ctypes.byref(num)),
+           "pf3_range_plan")
+    out = dict(zip(RANGE_PLAN_FIELDS, (int(x) for x in info)))
+    out["chunks"] = list(zip((int(x) for x in cf[:num.value]), (int(x) for x in cl[:num.value])))
+    return out
+
+
 PLAN_KINDS = ("whole", "piece", "packed", "lane")
 
 
@@ -528,5 +552,6 @@ def exported_symbols() -> list[str]:
                         "pf3_cancel_queued", "pf3_longrun", "pf3_longrun_cancel",
                         "pf3_count_exhaustive", "pf3_variant_info", "pf3_vec_op",
                         "pf3_vec_unpack", "pf3_set_batch_tuning", "pf3_get_batch_tuning",
-                        "pf3_autotune_ex", "pf3_batch_plan", "pf3_variant_threads")
+                        "pf3_autotune_ex", "pf3_batch_plan", "pf3_variant_threads",
+                        "pf3_range_plan")
             if hasattr(_lib, n)]
