@@ -93,6 +93,20 @@ def replay_fifo(trace, arrivals):
     return results, lat, makespan
 
 
+def measure_capacity(n: int = 36, reps: int = 3) -> float:
+    """Gray subsets per second of the single-matrix walk on this GPU: the
+    best of `reps` full walks of the seeded uniform n x n matrix, after one
+    warm-up (a 36 x 36 walk takes about 9 ms on a GB300)."""
+    A = inputs.uniform_matrix(n, n)
+    binding.perm_f3(A)
+    best = float("inf")
+    for _ in range(reps):
+        t = time.perf_counter()
+        binding.perm_f3(A)
+        best = min(best, time.perf_counter() - t)
+    return float(1 << n) / best
+
+
 def run(jobs=5000, nmin=12, nmax=32, rho=0.7, seed=inputs.SEED_SERVE, capacity=None, fifo=True,
         cfg_overrides=None):
     trace = make_trace(seed, jobs, nmin, nmax)
@@ -100,7 +114,7 @@ def run(jobs=5000, nmin=12, nmax=32, rho=0.7, seed=inputs.SEED_SERVE, capacity=N
     work = float(sum(1 << n for n in ns))
     mean_work = float(np.mean([(1 << n) for n in range(nmin, nmax + 1)]))
     if capacity is None:
-        capacity = 5.0e12
+        capacity = measure_capacity()
     rate = rho * capacity / mean_work
     arrivals = inputs.poisson_arrivals(seed, jobs, rate)
     res, lat, makespan, stats = replay(trace, arrivals, cfg_overrides)
@@ -122,7 +136,8 @@ def main():
     ap.add_argument("--nmin", type=int, default=12)
     ap.add_argument("--nmax", type=int, default=32)
     ap.add_argument("--rho", type=float, default=0.7)
-    ap.add_argument("--capacity", type=float, default=None)
+    ap.add_argument("--capacity", type=float, default=None,
+                    help="subsets/s the offered load is scaled to (default: measured on a 36x36 walk)")
     ap.add_argument("--no-fifo", action="store_true")
     ap.add_argument("--oldest-share", type=int, default=None, help="percent of each launch for the oldest request")
     ap.add_argument("--chunk-log2", type=int, default=None)
