@@ -84,3 +84,73 @@ def test_header_is_c99_and_links(tmp_path, libpath):
                     str(exe), "-L", libdir, "-lperm_f3", f"-Wl,-rpath,{libdir}"], check=True, capture_output=True,
                    text=True)
     assert exe.exists()
+
+
+def _declarations():
+    """(return type, name, [parameter types]) of every function in the header."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    text = "\n".join(l for l in text.splitlines() if not l.strip().startswith("#"))
+    text = text.replace('extern "C" {', "")
+    out = []
+    for stmt in text.split(";"):
+        stmt = " ".join(stmt.split())
+        if not stmt or stmt.startswith(("typedef", "struct", "}", "extern")) or "{" in stmt:
+            stmt = stmt.split("}")[-1].strip() if "}" in stmt else stmt
+            if not stmt or stmt.startswith(("typedef", "struct", "extern")):
+                continue
+        m = re.match(r"^(.*?)\b([a-z][a-z0-9_]*)\s*\((.*)\)$", stmt)
+        if not m:
+            continue
+        ret, name, params = m.group(1).strip(), m.group(2), m.group(3).strip()
+        plist = [] if params in ("", "void") else [p.strip() for p in params.split(",")]
+        types = []
+        for p in plist:
+            if "*" in p:
+                types.append("ptr")
+            else:
+                types.append(" ".join(p.split()[:-1]).replace("const ", ""))
+        out.append(("ptr" if "*" in ret else ret.replace("const ", "").strip(), name, types))
+    return out
+
+
+def test_binding_signatures_match_the_header(libpath):
+    """Every function the ctypes layer declares has the header's parameter
+    count, pointer/scalar kinds, integer widths and return type: a mismatch
+    would pass garbage through the ABI without any error."""
+    import ctypes
+    from paper_2407_20205_gb300 import binding
+    scalar = {"int": ctypes.c_int, "int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64,
+              "uint64_t": ctypes.c_uint64, "double": ctypes.c_double}
+    decl = {name: (ret, types) for ret, name, types in _declarations()}
+    assert len(decl) >= 40, sorted(decl)
+    checked = 0
+    for attr in dir(binding):
+        f = getattr(binding, attr)
+        name = getattr(f, "__name__", None)
+        if not attr.startswith("_lib_") or name not in decl:
+            continue
+        ret, types = decl[name]
+        argtypes = list(f.argtypes or [])
+        assert len(argtypes) == len(types), (name, types, argtypes)
+        for t, a in zip(types, argtypes):
+            if t == "ptr":
+                assert a in (ctypes.c_void_p, ctypes.c_char_p) or hasattr(a, "_type_") and \
+                    issubclass(a, ctypes._Pointer), (name, t, a)
+            else:
+                assert ctypes.sizeof(a) == ctypes.sizeof(scalar[t]), (name, t, a)
+                if t in ("int", "int32_t", "int64_t"):
+                    assert a(-1).value == -1, (name, t, a)   # signed
+                if t == "uint64_t":
+                    assert a(-1).value > 0, (name, t, a)     # unsigned
+                if t == "double":
+                    assert a is ctypes.c_double, (name, t, a)
+        if ret == "ptr":
+            assert f.restype in (ctypes.c_char_p, ctypes.c_void_p), (name, f.restype)
+        elif ret == "void":
+            assert f.restype is None, (name, f.restype)
+        else:
+            assert ctypes.sizeof(f.restype) == ctypes.sizeof(scalar[ret]), (name, ret, f.restype)
+        checked += 1
+    assert checked >= 35, checked
