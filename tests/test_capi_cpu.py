@@ -154,3 +154,30 @@ def test_binding_signatures_match_the_header(libpath):
             assert ctypes.sizeof(f.restype) == ctypes.sizeof(scalar[ret]), (name, ret, f.restype)
         checked += 1
     assert checked >= 35, checked
+
+
+def test_struct_layouts_match_the_binding(tmp_path):
+    """sizeof and every field offset of the header's structs, as a C99
+    compiler lays them out, equal the ctypes Structures the binding passes."""
+    import ctypes
+    from paper_2407_20205_gb300 import binding
+    structs = {"pf3_config": binding.PF3Config, "pf3_plan_item": binding.PlanItem}
+    lines = []
+    for cname, cls in structs.items():
+        lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
+        for field, _ in cls._fields_:
+            lines.append(f'    printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "perm_f3.h"\nint main(void) {\n'
+                   + "\n".join(lines) + "\n    return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True, capture_output=True, text=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        cname, what, val = line.split()
+        got[(cname, what)] = int(val)
+    for cname, cls in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for field, _ in cls._fields_:
+            assert got[(cname, field)] == getattr(cls, field).offset, (cname, field)
