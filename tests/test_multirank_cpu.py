@@ -75,10 +75,10 @@ def _worker_recovery(rank, world, port, n, seed, out_path, die_rank):
     if rank == 0:
         with open(out_path, "w") as f:
             f.write(f"{res['plus']} {res['minus']} {','.join(map(str, res['recovered']))}")
-        # keep the store (hosted by rank 0) up until the other rank is done
-        store.wait(["done/1"])
+        # keep the store (hosted by rank 0) up until the other ranks are done
+        store.wait([f"done/{r}" for r in range(1, world)])
     else:
-        store.set("done/1", "1")
+        store.set(f"done/{rank}", "1")
 
 
 def test_gloo_rank_failure_is_recovered(tmp_path, oracle):
@@ -93,3 +93,28 @@ def test_gloo_rank_failure_is_recovered(tmp_path, oracle):
     A = inputs.uniform_matrix(seed, n)
     assert (P, M) == oracle.counts(np.ascontiguousarray(A.T))
     assert recovered == [3, 5]  # rank 1 owns chunks 1, 3, 5 and published only chunk 1
+
+
+def test_gloo_three_ranks_uneven_split(tmp_path, oracle):
+    """2^13 Gray indices over 3 ranks (an uneven split): the all-reduced counts
+    equal the oracle's whole walk."""
+    n, seed = 13, 1503
+    out = str(tmp_path / "res.txt")
+    mp.start_processes(_worker_allreduce, args=(3, free_port(), n, seed, out), nprocs=3, start_method="spawn")
+    P, M = (int(x) for x in open(out).read().split())
+    A = inputs.uniform_matrix(seed, n)
+    assert (P, M) == oracle.counts(np.ascontiguousarray(A.T))
+
+
+def test_gloo_three_ranks_last_rank_fails(tmp_path, oracle):
+    """With 3 ranks and 3 chunks each, rank 2 owns chunks 2, 5, 8 and stops
+    after publishing chunk 2; rank 0 recomputes 5 and 8 at the deadline."""
+    n, seed = 14, 1504
+    out = str(tmp_path / "res.txt")
+    mp.start_processes(_worker_recovery, args=(3, free_port(), n, seed, out, 2), nprocs=3, start_method="spawn")
+    fields = open(out).read().split()
+    P, M = int(fields[0]), int(fields[1])
+    recovered = [int(x) for x in fields[2].split(",")] if len(fields) > 2 else []
+    A = inputs.uniform_matrix(seed, n)
+    assert (P, M) == oracle.counts(np.ascontiguousarray(A.T))
+    assert recovered == [5, 8]
