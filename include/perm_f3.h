@@ -55,6 +55,9 @@ extern "C" {
 #define PF3_ETOOBIG (-8)     /* request larger than a fixed buffer: no-allocation scratch, output array */
 
 #define PF3_MAX_N 64
+/* Most matrices in one batch call (work items index matrices with 32-bit
+ * integers); larger counts are rejected with PF3_EINVAL. */
+#define PF3_MAX_BATCH 2147483583LL
 
 /* Human-readable text for a return code (static storage). */
 const char* pf3_strerror(int code);
@@ -130,7 +133,8 @@ void pf3_longrun_cancel(int on);
  * back, matrix k (size ns[k] x ns[k]) starting at byte sum_{j<k} ns[j]^2.
  * results: host, count bytes.  hist: optional host uint64[3], the number of
  * results equal to 0, 1 and 2 (the Monte Carlo statistic of Sec. 4).  Matrices
- * of different n may be mixed.  Returns 0 or a negative code. */
+ * of different n may be mixed.  0 <= count <= PF3_MAX_BATCH.  Returns 0 or a
+ * negative code. */
 int perm_f3_batch(const uint8_t* As, const int32_t* ns, int64_t count, uint8_t* results, uint64_t* hist);
 
 /* Device-pointer batch: dAs, d_results (count bytes) and d_hist (3 x uint64,
@@ -140,7 +144,7 @@ int perm_f3_batch(const uint8_t* As, const int32_t* ns, int64_t count, uint8_t* 
  * launch sequence (item-table upload, counter resets, one persistent kernel
  * per plane width) is captured as a CUDA graph; a later call with the same ns,
  * pointers and tuning replays the graph without re-planning, reading the
- * current contents of dAs. */
+ * current contents of dAs.  0 <= count <= PF3_MAX_BATCH. */
 int perm_f3_batch_async(const uint8_t* dAs, const int32_t* ns, int64_t count, uint8_t* d_results,
                         uint64_t* d_hist, void* stream);
 

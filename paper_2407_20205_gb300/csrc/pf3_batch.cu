@@ -559,7 +559,9 @@ int pf3_batch_plan(const int32_t* ns, int64_t count, int tiny_cutoff, int split_
                    int items_per_warp, const int* variant, const int* warps, pf3_plan_item* items, int64_t capacity,
                    int64_t* num_items, int* auto_chunk_log2)
 {
-    if (count < 0 || (count > 0 && !ns) || !variant || !warps || !num_items || capacity < 0) return PF3_EINVAL;
+    if (count < 0 || count > PF3_MAX_BATCH || (count > 0 && !ns) || !variant || !warps || !num_items ||
+        capacity < 0)
+        return PF3_EINVAL;
     if (tiny_cutoff < 0 || tiny_cutoff > kTinyMaxN || split_cutoff < 0 || split_cutoff > PF3_MAX_N ||
         (chunk_log2 != 0 && (chunk_log2 < 12 || chunk_log2 > 62)) || items_per_warp < 1 || items_per_warp > 1024)
         return PF3_EINVAL;
@@ -604,7 +606,7 @@ int pf3_batch_plan(const int32_t* ns, int64_t count, int tiny_cutoff, int split_
 
 int perm_f3_batch(const uint8_t* As, const int32_t* ns, int64_t count, uint8_t* results, uint64_t* hist)
 {
-    if (count < 0 || (count > 0 && (!ns || !results))) return PF3_EINVAL;
+    if (count < 0 || count > PF3_MAX_BATCH || (count > 0 && (!ns || !results))) return PF3_EINVAL;
     if (count == 0) {
         if (hist) hist[0] = hist[1] = hist[2] = 0;
         return PF3_OK;
@@ -649,7 +651,7 @@ int perm_f3_batch(const uint8_t* As, const int32_t* ns, int64_t count, uint8_t* 
 int perm_f3_batch_async(const uint8_t* dAs, const int32_t* ns, int64_t count, uint8_t* d_results, uint64_t* d_hist,
                         void* stream)
 {
-    if (count < 0 || (count > 0 && (!ns || !d_results))) return PF3_EINVAL;
+    if (count < 0 || count > PF3_MAX_BATCH || (count > 0 && (!ns || !d_results))) return PF3_EINVAL;
     size_t bytes = 0;
     for (int64_t k = 0; k < count; ++k) {
         if (ns[k] < 0 || ns[k] > PF3_MAX_N) return PF3_EINVAL;

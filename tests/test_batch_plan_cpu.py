@@ -156,3 +156,16 @@ def test_plan_rejects_bad_arguments():
     with pytest.raises(pf3.PF3Error):
         pf3.batch_plan([5], warps=(0, 1))
     assert pf3.batch_plan([], warps=(1, 1))["items"] == []
+
+
+def test_batch_counts_beyond_32_bit_indices_are_rejected():
+    """Work items index matrices with 32-bit integers, so a count above
+    PF3_MAX_BATCH (2^31 - 65) is refused before anything is read."""
+    import ctypes
+    va = (ctypes.c_int * 2)(0, 0)
+    wa = (ctypes.c_int * 2)(2432, 2432)
+    num = ctypes.c_int64()
+    for count in (2**31 - 64, 2**40):
+        rc = pf3._lib_plan(None, count, 10, 28, 0, 8, va, wa, None, 0, ctypes.byref(num), None)
+        assert rc == pf3.PF3_EINVAL
+        assert pf3._lib_batch(None, None, count, None, None) == pf3.PF3_EINVAL
