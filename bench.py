@@ -316,9 +316,9 @@ def run_ours(args):
             torch.distributed.all_reduce(counts[n])
     results = {}
     for n in SIZES:
-        p, m = [int(x) for x in counts[n].cpu()]
-        d = (p - m) * (-1 if n & 1 else 1)
-        results[n] = d % 3
+        # the counts are uint64 carried in int64 tensors: read the bits back unsigned
+        p, m = [int(x) % (1 << 64) for x in counts[n].cpu()]
+        results[n] = pf3.perm_from_counts(n, p, m)
     subsets_step = sum(1 << n for n in SIZES)
     value = subsets_step * args.steps / (total_ms * 1e-3)
 

@@ -29,8 +29,12 @@
  *   - Device-pointer entry points (suffix _async) are stream-ordered on the
  *     given cudaStream_t (NULL = legacy default stream); they return once the
  *     work is enqueued.  The caller owns every pointer passed in.  They share
- *     the device's scratch, so two _async calls must not overlap on the GPU
- *     (use one stream, or order the streams).
+ *     the device's scratch with each other and with the host-pointer calls;
+ *     the library orders every use of it after the previous one (an event
+ *     recorded after each launch, waited for by the next, on whatever
+ *     stream), so calls on different streams are correct but do not run
+ *     concurrently.  Inside a stream capture that ordering is left out and
+ *     the capturing caller must order the calls itself.
  *   - Return value: >= 0 on success, a negative PF3_E* code on failure.
  */
 #ifndef PERM_F3_H
@@ -71,6 +75,14 @@ const char* pf3_version(void);
  * or a negative PF3_E* code. */
 int perm_f3(const uint8_t* A, int n);
 
+/* The final map of Eq. (2) (with the closing cmod3 of Sec. 3): perm(A) =
+ * (-1)^n (plus - minus) mod 3, returned in {0,1,2}, for the exact term counts
+ * of an n x n matrix (sums of perm_f3_range_counts over disjoint ranges, e.g.
+ * from several processes).  Counts are unsigned 64-bit: each is reduced mod 3
+ * on its own, so counts of 2^63 and above (n = 64) are exact.  Host only; no
+ * device is touched.  PF3_EINVAL when n is outside 0..64. */
+int pf3_perm_from_counts(int n, uint64_t plus, uint64_t minus);
+
 /* Term counts over all 2^n Gray indices (the exact sum behind perm_f3).
  * plus/minus: host outputs.  For n = 0, plus = 1 and minus = 0. */
 int perm_f3_counts(const uint8_t* A, int n, uint64_t* plus, uint64_t* minus);
@@ -102,15 +114,21 @@ int perm_f3_range_counts_async(const uint8_t* dA, int n, uint64_t first, uint64_
  * cudaMalloc or cudaFree.  ctas: CTAs to launch, 0 = one resident wave;
  * values above PF3_NOALLOC_MAX_CTAS are rejected with PF3_ETOOBIG.  The first
  * call on each device looks up the array's device address and the kernel's
- * occupancy; make that first call before any stream capture.  All calls on a
- * device share the array (each call clears its flags first): calls that
- * overlap on the GPU race and must be ordered by the caller. */
+ * occupancy; make that first call before any stream capture.  That address
+ * is kept for the life of the process: after a cudaDeviceReset by the caller
+ * it is stale, so a process that resets a device must not call this entry
+ * point on it again.  All calls on a device share the array (each call clears
+ * its flags first): calls that overlap on the GPU race and must be ordered by
+ * the caller. */
 #define PF3_NOALLOC_MAX_CTAS 1024
 int perm_f3_range_counts_noalloc(const uint8_t* dA, int n, uint64_t first, uint64_t last, uint64_t* d_out,
                                  int ctas, void* stream);
 
 /* Long walks in bounded launches (Sec. 3.1's split of the Gray range into
- * jobs, here consecutive launches of at most 2^chunk_log2 indices each).
+ * jobs, here consecutive launches of at most 2^chunk_log2 indices each,
+ * 10 <= chunk_log2 <= PF3_LONGRUN_MAX_CHUNK_LOG2, so that one launch lasts
+ * seconds at most and cancellation and max_seconds are seen often).  The
+ * device is held for one launch at a time: other calls on it interleave.
  * After every launch the exact counts and the next Gray index are written to
  * checkpoint_path (temporary file + rename; NULL = no checkpoint).  If the
  * file already holds a checkpoint of the same matrix, the walk resumes from
@@ -119,9 +137,11 @@ int perm_f3_range_counts_noalloc(const uint8_t* dA, int n, uint64_t first, uint6
  * after each launch, so every call makes at least one launch of progress) or
  * when pf3_longrun_cancel(1) was called (PF3_ECANCELED; checked before each
  * launch); the counts so far are returned and saved either way.  *finished = 1 once the whole range is done;
- * *next_index is the first index not yet walked (0 when finished). */
+ * *next_index is the first index not yet walked (0 when finished).  result
+ * (may be NULL): perm(A) mod 3 in {0,1,2} once finished, untouched before. */
+#define PF3_LONGRUN_MAX_CHUNK_LOG2 44
 int pf3_longrun(const uint8_t* A, int n, int chunk_log2, const char* checkpoint_path, double max_seconds,
-                uint64_t* plus, uint64_t* minus, uint64_t* next_index, int* finished);
+                uint64_t* plus, uint64_t* minus, uint64_t* next_index, int* finished, int* result);
 
 /* Set (1) or clear (0) the flag that makes pf3_longrun stop at its next
  * launch boundary; callable from any thread. */

@@ -40,9 +40,8 @@ def main(argv=None):
     elif cmd == "counts":
         A = read_matrix(argv[1] if len(argv) > 1 else "-")
         p, m = binding.perm_f3_counts(A)
-        d = p - m
         print(json.dumps({"n": int(A.shape[0]), "plus": p, "minus": m,
-                          "perm": (-d if A.shape[0] & 1 else d) % 3}))
+                          "perm": binding.perm_from_counts(int(A.shape[0]), p, m)}))
     elif cmd == "random":
         n, seed = int(argv[1]), int(argv[2])
         for row in inputs.uniform_matrix(seed, n):

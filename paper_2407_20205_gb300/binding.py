@@ -158,6 +158,15 @@ def perm_f3(A) -> int:
     return _check(_lib_perm(p, n), "perm_f3")
 
 
+_lib_from_counts = _sig("pf3_perm_from_counts", ctypes.c_int, [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64])
+
+
+def perm_from_counts(n: int, plus: int, minus: int) -> int:
+    """perm mod 3 in {0,1,2} from exact (plus, minus) term counts of an n x n
+    matrix (the library's final map; counts are unsigned 64-bit)."""
+    return _check(_lib_from_counts(n, plus, minus), "pf3_perm_from_counts")
+
+
 def perm_f3_counts(A) -> tuple[int, int]:
     """(plus, minus) Ryser term counts over all 2^n Gray indices."""
     a, p, n = _square(A)
@@ -238,7 +247,9 @@ def count_exhaustive(n: int) -> tuple[int, int, int]:
 # ------------------------------------------------------------ long runs
 
 _lib_longrun = _sig("pf3_longrun", ctypes.c_int,
-                    [_u8p, ctypes.c_int, ctypes.c_int, ctypes.c_char_p, ctypes.c_double, _u64p, _u64p, _u64p, _ip])
+                    [_u8p, ctypes.c_int, ctypes.c_int, ctypes.c_char_p, ctypes.c_double, _u64p, _u64p, _u64p, _ip,
+                     _ip])
+LONGRUN_MAX_CHUNK_LOG2 = 44
 _lib_longrun_cancel = _sig("pf3_longrun_cancel", None, [ctypes.c_int])
 
 
@@ -247,15 +258,14 @@ def longrun(A, chunk_log2: int = 42, checkpoint: str | None = None, max_seconds:
     after each; returns counts, progress and the return code (PF3_OK,
     PF3_ETIMEDOUT or PF3_ECANCELED leave a resumable checkpoint)."""
     a, p, n = _square(A)
-    P, M, nxt, fin = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_int()
+    P, M, nxt, fin, res_ = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_int(), ctypes.c_int(-1)
     rc = _lib_longrun(p, n, chunk_log2, checkpoint.encode() if checkpoint else None, max_seconds,
-                      ctypes.byref(P), ctypes.byref(M), ctypes.byref(nxt), ctypes.byref(fin))
+                      ctypes.byref(P), ctypes.byref(M), ctypes.byref(nxt), ctypes.byref(fin), ctypes.byref(res_))
     if rc < 0 and rc not in (PF3_ETIMEDOUT, PF3_ECANCELED):
         raise PF3Error(rc, "pf3_longrun")
     res = {"rc": rc, "plus": P.value, "minus": M.value, "next_index": nxt.value, "finished": bool(fin.value)}
     if fin.value:
-        d = P.value - M.value
-        res["perm"] = (-d if n & 1 else d) % 3
+        res["perm"] = int(res_.value)
     return res
 
 
@@ -553,5 +563,5 @@ def exported_symbols() -> list[str]:
                         "pf3_count_exhaustive", "pf3_variant_info", "pf3_vec_op",
                         "pf3_vec_unpack", "pf3_set_batch_tuning", "pf3_get_batch_tuning",
                         "pf3_autotune_ex", "pf3_batch_plan", "pf3_variant_threads",
-                        "pf3_range_plan")
+                        "pf3_range_plan", "pf3_perm_from_counts")
             if hasattr(_lib, n)]

@@ -483,6 +483,17 @@ static bool same_tuning(const BatchTuning& a, const BatchTuning& b)
            a.items_per_warp == b.items_per_warp && a.variant[0] == b.variant[0] && a.variant[1] == b.variant[1];
 }
 
+// Launch the instantiated graph on `stream`, after the previous replay (on
+// any stream) has finished with the graph's buffers.
+static int launch_batch_graph(DeviceCtx* c, cudaStream_t stream)
+{
+    bool capturing = false;
+    int rc = scratch_acquire(c->bgraph_free, stream, &capturing);
+    if (rc) return rc;
+    if ((rc = cuda_rc(cudaGraphLaunch(c->bgraph.exec, stream)))) return rc;
+    return scratch_release(c->bgraph_free, stream, capturing);
+}
+
 // Replay the captured launch sequence when nothing changed, else plan,
 // capture on a private stream, instantiate and launch.
 int enqueue_batch_graph(DeviceCtx* c, const int32_t* ns, int64_t count, const uint8_t* dAs, uint8_t* d_results,
@@ -491,9 +502,11 @@ int enqueue_batch_graph(DeviceCtx* c, const int32_t* ns, int64_t count, const ui
     BatchGraphCache& g = c->bgraph;
     if (g.valid && (int64_t)g.ns.size() == count && g.dAs == dAs && g.d_results == d_results && g.d_hist == d_hist &&
         same_tuning(g.tune, c->tune) && std::memcmp(g.ns.data(), ns, (size_t)count * sizeof(int32_t)) == 0)
-        return cuda_rc(cudaGraphLaunch(g.exec, stream));
-    // a previous replay may still read the buffers about to be freed
+        return launch_batch_graph(c, stream);
+    // a previous replay, on this or another stream, may still read the
+    // buffers about to be freed
     cudaError_t e = cudaStreamSynchronize(stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(c->bgraph_free);
     if (e != cudaSuccess) return cuda_rc(e);
     if (g.valid || g.exec) free_graph(g);
     BatchPlan plan;
@@ -546,7 +559,7 @@ int enqueue_batch_graph(DeviceCtx* c, const int32_t* ns, int64_t count, const ui
     g.n_items[1] = (int)n1;
     g.num_split = plan.num_split;
     g.valid = true;
-    return cuda_rc(cudaGraphLaunch(g.exec, stream));
+    return launch_batch_graph(c, stream);
 }
 
 }  // namespace pf3

@@ -68,6 +68,8 @@ DeviceCtx* device_ctx(int* rc)
     ok = ok && cudaMalloc(&c->d_flags, sizeof(unsigned int) * 4) == cudaSuccess;
     ok = ok && cudaMalloc(&c->d_out, sizeof(unsigned long long) * 4) == cudaSuccess;
     ok = ok && cudaMemset(c->d_flags, 0, sizeof(unsigned int) * 4) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&c->scratch_free, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&c->bgraph_free, cudaEventDisableTiming) == cudaSuccess;
     ok = ok && cudaMallocHost(&c->h_A, kMaxNN) == cudaSuccess;
     ok = ok && cudaMallocHost(&c->h_out, sizeof(unsigned long long) * 4) == cudaSuccess;
     ok = ok && cudaDeviceSynchronize() == cudaSuccess;
@@ -80,6 +82,22 @@ DeviceCtx* device_ctx(int* rc)
     g_ctx[dev] = c;
     *rc = PF3_OK;
     return c;
+}
+
+int scratch_acquire(cudaEvent_t ev, cudaStream_t stream, bool* capturing)
+{
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(stream, &st);
+    if (e != cudaSuccess) return cuda_rc(e);
+    *capturing = st != cudaStreamCaptureStatusNone;
+    if (*capturing) return PF3_OK;
+    return cuda_rc(cudaStreamWaitEvent(stream, ev, 0));
+}
+
+int scratch_release(cudaEvent_t ev, cudaStream_t stream, bool capturing)
+{
+    if (capturing) return PF3_OK;
+    return cuda_rc(cudaEventRecord(ev, stream));
 }
 
 int single_ctas(DeviceCtx* c, int W, int v) { return c->single_ctas[W - 1][v]; }
@@ -110,7 +128,12 @@ int enqueue_range(DeviceCtx* c, const uint8_t* dA, int n, uint64_t first, uint64
     a.cursor = c->d_flags + 2;
     a.out = d_out;
     const int grid = single_grid_for(a, v, c->sm_count, single_ctas(c, W, v));
-    return cuda_rc(launch_single(a, v, grid, stream));
+    // the partials and flags are shared by every call on this device
+    bool capturing = false;
+    int rc = scratch_acquire(c->scratch_free, stream, &capturing);
+    if (rc) return rc;
+    if ((rc = cuda_rc(launch_single(a, v, grid, stream)))) return rc;
+    return scratch_release(c->scratch_free, stream, capturing);
 }
 
 int valid_range(int n, uint64_t first, uint64_t last)
@@ -180,6 +203,12 @@ int perm_f3(const uint8_t* A, int n)
     return rc ? rc : result;
 }
 
+int pf3_perm_from_counts(int n, uint64_t plus, uint64_t minus)
+{
+    if (n < 0 || n > PF3_MAX_N) return PF3_EINVAL;
+    return (int)perm_from_counts(n, plus, minus);
+}
+
 int perm_f3_counts(const uint8_t* A, int n, uint64_t* plus, uint64_t* minus)
 {
     if (!plus || !minus || n < 0 || n > PF3_MAX_N) return PF3_EINVAL;
@@ -240,12 +269,18 @@ int pf3_pack(const uint8_t* A, int n, uint64_t* mag, uint64_t* sgn)
     if (e != cudaSuccess) return cuda_rc(e);
     const size_t nn = (size_t)n * n;
     std::memcpy(c->h_A, A, nn);
+    bool capturing = false;
+    if ((rc = scratch_acquire(c->scratch_free, c->stream, &capturing))) {
+        cudaFree(d);
+        return rc;
+    }
     e = cudaMemcpyAsync(c->d_A, c->h_A, nn, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = launch_pack(c->d_A, n, d, d + PF3_MAX_N, c->d_flags + 1, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(mag, d, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(sgn, d + PF3_MAX_N, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_flags + 1, 0, sizeof(unsigned int), c->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(c->scratch_free, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     cudaFree(d);
     return cuda_rc(e);

@@ -66,6 +66,13 @@ struct DeviceCtx {
     unsigned long long* d_out = nullptr;      // plus, minus, result
     uint8_t* h_A = nullptr;                   // pinned
     unsigned long long* h_out = nullptr;      // pinned
+    // Recorded on the launching stream after every launch that uses
+    // d_partials/d_flags; the next such launch, on whatever stream, waits for
+    // it first, so calls on different streams never share the scratch at the
+    // same time.  bgraph_free does the same for the captured batch graph's
+    // buffers.
+    cudaEvent_t scratch_free = nullptr;
+    cudaEvent_t bgraph_free = nullptr;
     BatchScratch batch;
     BatchGraphCache bgraph;
     cudaStream_t capture_stream = nullptr;
@@ -75,6 +82,12 @@ struct DeviceCtx {
 
 int cuda_rc(cudaError_t e);
 DeviceCtx* device_ctx(int* rc);
+// Order work on `stream` that uses the buffers guarded by `ev` after the
+// previous user of those buffers (cudaStreamWaitEvent), and mark its end
+// (cudaEventRecord).  Inside a stream capture both do nothing: ordering the
+// captured work is then the capturing caller's job.
+int scratch_acquire(cudaEvent_t ev, cudaStream_t stream, bool* capturing);
+int scratch_release(cudaEvent_t ev, cudaStream_t stream, bool capturing);
 int check_entries_host(const uint8_t* A, int n);
 int single_ctas(DeviceCtx* c, int W, int v);
 void load_tune_cache(DeviceCtx* c);

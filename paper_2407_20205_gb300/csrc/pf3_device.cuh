@@ -519,14 +519,6 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v)
     return v;
 }
 
-// (-1)^n (plus - minus) mod 3, in {0,1,2} (Eq. (2) with the final cmod3 of Sec. 3)
-__device__ __forceinline__ uint32_t perm_from_counts(int n, unsigned long long plus, unsigned long long minus)
-{
-    int d = (int)(plus % 3ull) - (int)(minus % 3ull);
-    if (n & 1) d = -d;
-    return (uint32_t)((d + 3) % 3);
-}
-
 }  // namespace pf3
 
 namespace pf3 {

@@ -7,6 +7,19 @@
 
 namespace pf3 {
 
+// The final map of Eq. (2): perm(A) = (-1)^n (plus - minus) mod 3, in
+// {0,1,2}, from the exact counts of +1 and -1 terms (the closing cmod3 of
+// Sec. 3).  Each count is reduced mod 3 on its own, so no signed difference
+// of two 64-bit counts is ever formed (both may exceed 2^63 at n = 64).  One
+// definition for the kernels' epilogues and the host entry point
+// pf3_perm_from_counts.
+__host__ __device__ inline uint32_t perm_from_counts(int n, unsigned long long plus, unsigned long long minus)
+{
+    int d = (int)(plus % 3ull) - (int)(minus % 3ull);
+    if (n & 1) d = -d;
+    return (uint32_t)((d + 3) % 3);
+}
+
 // A compiled variant of a walk kernel: probe groups of 2^G Gray indices,
 // unrolled blocks of 2^U indices, the minimum resident CTAs per SM it was
 // compiled for (its register budget) and its CTA size.
@@ -56,6 +69,32 @@ struct SingleArgs {
     unsigned int* cursor;          // device scratch, 0 between launches
     unsigned long long* out;       // device: plus, minus, result (~0 on bad entry)
 };
+
+// Chunk k < nchunks of the middle blocks, relative to mid_B0 (Sec. 3.1's
+// blocks of consecutive Gray states, handed to warps in guided phases): phase
+// j is per_phase chunks of len0 >> j blocks (rounded down to a multiple of 32)
+// while that is at least tail_len, then chunks of tail_len blocks up to
+// mid_NB.  One definition for the kernel, which calls it for the chunk index
+// it took from the cursor, and for the host planner that lists the chunks; at
+// most one turn of the loop per guided phase (the length halves each turn).
+__host__ __device__ inline void chunk_range(const SingleArgs& a, unsigned k, uint64_t& start, uint64_t& len)
+{
+    uint64_t s = 0, L = a.len0;
+    while (L >= a.tail_len) {
+        if (k < a.per_phase) {
+            start = s + (uint64_t)k * L;
+            const uint64_t left = a.mid_NB - start;
+            len = left < L ? left : L;
+            return;
+        }
+        s += (uint64_t)a.per_phase * L;
+        k -= a.per_phase;
+        L = (L >> 1) & ~31ull;
+    }
+    start = s + (uint64_t)k * a.tail_len;
+    const uint64_t left = a.mid_NB - start;
+    len = left < a.tail_len ? left : a.tail_len;
+}
 
 // split [first, last] into a ragged head, aligned middle blocks of 2^U
 // indices and a ragged tail

@@ -88,9 +88,10 @@ extern "C" {
 void pf3_longrun_cancel(int on) { g_cancel.store(on ? 1 : 0); }
 
 int pf3_longrun(const uint8_t* A, int n, int chunk_log2, const char* checkpoint_path, double max_seconds,
-                uint64_t* plus, uint64_t* minus, uint64_t* next_index, int* finished)
+                uint64_t* plus, uint64_t* minus, uint64_t* next_index, int* finished, int* result)
 {
-    if (!A || n < 1 || n > PF3_MAX_N || chunk_log2 < 10 || chunk_log2 > 64 || !plus || !minus)
+    if (!A || n < 1 || n > PF3_MAX_N || chunk_log2 < 10 || chunk_log2 > PF3_LONGRUN_MAX_CHUNK_LOG2 || !plus ||
+        !minus)
         return PF3_EINVAL;
     int rc = check_entries_host(A, n);
     if (rc) return rc;
@@ -108,13 +109,9 @@ int pf3_longrun(const uint8_t* A, int n, int chunk_log2, const char* checkpoint_
         ck.hash = hash;
     }
     const uint64_t last = (n == 64) ? ~0ull : ((1ull << n) - 1);
-    const uint64_t step_m1 = (chunk_log2 >= 64) ? ~0ull : ((1ull << chunk_log2) - 1);
+    const uint64_t step_m1 = (1ull << chunk_log2) - 1;
     const auto t0 = std::chrono::steady_clock::now();
-    std::lock_guard<std::mutex> g(c->mu);
     const size_t nn = (size_t)n * n;
-    std::memcpy(c->h_A, A, nn);
-    cudaError_t e = cudaMemcpyAsync(c->d_A, c->h_A, nn, cudaMemcpyHostToDevice, c->stream);
-    rc = cuda_rc(e);
     while (!rc && !ck.done) {
         if (g_cancel.load()) {
             rc = PF3_ECANCELED;
@@ -122,12 +119,22 @@ int pf3_longrun(const uint8_t* A, int n, int chunk_log2, const char* checkpoint_
         }
         const uint64_t first = ck.cursor;
         const uint64_t stop = (last - first <= step_m1) ? last : first + step_m1;
-        if ((rc = enqueue_range(c, c->d_A, n, first, stop, c->d_out, c->stream))) break;
-        e = cudaMemcpyAsync(c->h_out, c->d_out, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        if ((rc = cuda_rc(e))) break;
-        ck.plus += c->h_out[0];
-        ck.minus += c->h_out[1];
+        {
+            // the device context is held for one launch at a time, so other
+            // calls on this device interleave with a long walk; the matrix is
+            // copied again each time because they share the staging buffers
+            std::lock_guard<std::mutex> g(c->mu);
+            std::memcpy(c->h_A, A, nn);
+            cudaError_t e = cudaMemcpyAsync(c->d_A, c->h_A, nn, cudaMemcpyHostToDevice, c->stream);
+            if ((rc = cuda_rc(e))) break;
+            if ((rc = enqueue_range(c, c->d_A, n, first, stop, c->d_out, c->stream))) break;
+            e = cudaMemcpyAsync(c->h_out, c->d_out, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            if ((rc = cuda_rc(e))) break;
+            ck.plus += c->h_out[0];
+            ck.minus += c->h_out[1];
+        }
         if (stop == last) ck.done = 1;
         else ck.cursor = stop + 1;
         if (checkpoint_path && !write_checkpoint(checkpoint_path, ck)) {
@@ -142,6 +149,7 @@ int pf3_longrun(const uint8_t* A, int n, int chunk_log2, const char* checkpoint_
     *minus = ck.minus;
     if (next_index) *next_index = ck.done ? 0 : ck.cursor;
     if (finished) *finished = ck.done;
+    if (result && ck.done) *result = (int)perm_from_counts(n, ck.plus, ck.minus);
     return rc;
 }
 

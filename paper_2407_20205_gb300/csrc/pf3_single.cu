@@ -23,27 +23,6 @@ namespace pf3 {
 
 namespace {
 
-// chunk k < nchunks of the middle blocks (relative to mid_B0): see
-// SingleArgs.  At most one turn per guided phase (the length halves each turn).
-__device__ __forceinline__ void chunk_range(const SingleArgs& a, unsigned k, uint64_t& start, uint64_t& len)
-{
-    uint64_t s = 0, L = a.len0;
-    while (L >= a.tail_len) {
-        if (k < a.per_phase) {
-            start = s + (uint64_t)k * L;
-            const uint64_t left = a.mid_NB - start;
-            len = left < L ? left : L;
-            return;
-        }
-        s += (uint64_t)a.per_phase * L;
-        k -= a.per_phase;
-        L = (L >> 1) & ~31ull;
-    }
-    start = s + (uint64_t)k * a.tail_len;
-    const uint64_t left = a.mid_NB - start;
-    len = left < a.tail_len ? left : a.tail_len;
-}
-
 template <int W, int U, int G, int MINB, int THREADS>
 __global__ void __launch_bounds__(THREADS, MINB) single_kernel(SingleArgs a)
 {

@@ -44,17 +44,31 @@ def chunks(n: int, count: int) -> list[tuple[int, int]]:
     return out
 
 
+_U64 = 1 << 64
+
+
+def _as_i64(x: int) -> int:
+    """The int64 with the same 64 bits as the uint64 x."""
+    return x - _U64 if x >= 1 << 63 else x
+
+
 def allreduce_counts(plus: int, minus: int, device=None) -> tuple[int, int]:
+    """Sum the two unsigned 64-bit counts over all ranks.  The collective
+    works on int64, so each count travels as the int64 with the same bits; a
+    two's-complement sum has the same bits as the unsigned sum mod 2^64, and
+    the true total of each count is below 2^64 (at most 2^n terms), so the
+    result read back as unsigned is exact even above 2^63."""
     import torch
     import torch.distributed as dist
-    t = torch.tensor([plus, minus], dtype=torch.int64, device=device)
+    t = torch.tensor([_as_i64(plus), _as_i64(minus)], dtype=torch.int64, device=device)
     dist.all_reduce(t)
-    return int(t[0]), int(t[1])
+    return int(t[0]) % _U64, int(t[1]) % _U64
 
 
 def perm_from_counts(n: int, plus: int, minus: int) -> int:
-    d = plus - minus
-    return (-d if n & 1 else d) % 3
+    """perm mod 3 from the summed counts: the library's final map."""
+    from . import binding
+    return binding.perm_from_counts(n, plus, minus)
 
 
 def walk_with_recovery(range_fn: RangeFn, n: int, rank: int, world: int, store, chunks_per_rank: int = 4,

@@ -181,3 +181,49 @@ def test_struct_layouts_match_the_binding(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(cls), cname
         for field, _ in cls._fields_:
             assert got[(cname, field)] == getattr(cls, field).offset, (cname, field)
+
+
+def test_perm_from_counts_matches_oracle(libpath, oracle):
+    """The library's final map of Eq. (2) (a host function: callable without a
+    GPU) against the oracle's, on counts up to 2^64 - 1 for every n, and its
+    refusal of n outside 0..64."""
+    import numpy as np
+    from paper_2407_20205_gb300 import binding
+    rng = np.random.default_rng(64)
+    edges = [0, 1, 2, 3, (1 << 63) - 1, 1 << 63, (1 << 63) + 1, (1 << 64) - 2, (1 << 64) - 1]
+    vals = edges + [int(x) for x in rng.integers(0, 1 << 63, 40, dtype=np.uint64)] + \
+        [(1 << 63) + int(x) for x in rng.integers(0, 1 << 63, 40, dtype=np.uint64)]
+    for n in range(0, 65):
+        for k in range(30):
+            p = vals[(7 * k + n) % len(vals)]
+            m = vals[(11 * k + 3 * n + 1) % len(vals)]
+            assert binding.perm_from_counts(n, p, m) == oracle.perm_from_counts(n, p, m), (n, p, m)
+    for bad in (-1, 65):
+        with pytest.raises(binding.PF3Error):
+            binding.perm_from_counts(bad, 1, 0)
+
+
+def test_no_mod3_arithmetic_in_python_package():
+    """The final map lives in the library: the Python package takes something
+    mod 3 only where it builds inputs (entries drawn or parsed into {0,1,2},
+    pi's digits into F3), never to turn counts into a permanent."""
+    import ast
+    allowed = {("inputs.py", None), ("pi_matrix.py", "digit_matrix"), ("__main__.py", "read_matrix")}
+    pkg = os.path.join(ROOT, "paper_2407_20205_gb300")
+    offenders = []
+    for f in sorted(os.listdir(pkg)):
+        if not f.endswith(".py"):
+            continue
+        tree = ast.parse(open(os.path.join(pkg, f)).read())
+        for fn in [None] + [x for x in ast.walk(tree) if isinstance(x, ast.FunctionDef)]:
+            body = tree if fn is None else fn
+            for node in ast.walk(body):
+                if (isinstance(node, ast.BinOp) and isinstance(node.op, ast.Mod)
+                        and isinstance(node.right, ast.Constant) and node.right.value == 3):
+                    owner = None
+                    for g in ast.walk(tree):
+                        if isinstance(g, ast.FunctionDef) and g.lineno <= node.lineno <= g.end_lineno:
+                            owner = g.name
+                    if (f, None) not in allowed and (f, owner) not in allowed:
+                        offenders.append(f"{f}:{node.lineno}")
+    assert not offenders, sorted(set(offenders))

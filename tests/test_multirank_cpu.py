@@ -118,3 +118,30 @@ def test_gloo_three_ranks_last_rank_fails(tmp_path, oracle):
     A = inputs.uniform_matrix(seed, n)
     assert (P, M) == oracle.counts(np.ascontiguousarray(A.T))
     assert recovered == [5, 8]
+
+
+def _worker_big_counts(rank, world, port, out_path):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    mine = [((1 << 63) + 5, (1 << 63) - 1), ((1 << 62) + 11, 3)][rank]
+    P, M = multirank.allreduce_counts(*mine)
+    if rank == 0:
+        with open(out_path, "w") as f:
+            f.write(f"{P} {M}")
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_gloo_counts_at_and_above_2_63(tmp_path, oracle):
+    """Counts of 2^63 and more (reachable at n = 64) survive the int64
+    collective exactly, and the library's final map of the sums agrees with
+    the oracle's on them (2^64 = 1 mod 3, so a wrapped sum would not)."""
+    out = str(tmp_path / "res.txt")
+    mp.start_processes(_worker_big_counts, args=(2, free_port(), out), nprocs=2, start_method="spawn")
+    P, M = (int(x) for x in open(out).read().split())
+    assert P == (1 << 63) + 5 + (1 << 62) + 11
+    assert M == (1 << 63) - 1 + 3
+    for n in (63, 64):
+        assert multirank.perm_from_counts(n, P, M) == oracle.perm_from_counts(n, P, M)
