@@ -9,12 +9,15 @@ through the host-pointer C entry point perm_f3 (input copied in, result
 copied out, every call).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--no-batch] [--no-cpu-baseline] [--no-serve] [--serve-jobs J] [--long]
+                  [--no-batch] [--no-cpu-baseline] [--no-serve] [--serve-jobs J]
+                  [--no-config1] [--no-long]
 
-Secondary measurements go under "extra": the batched Monte Carlo workload
-(200,000 seeded 24 x 24 matrices in one call, against the same matrices one
-launch each), the serving mix (Poisson arrivals, n in 12..40, against FIFO one
-matrix per launch) and, with --long, the seeded 48 x 48 matrix.
+Secondary measurements go under "extra": the seeded 20 x 20 matrix (one
+launch per permanent), the batched Monte Carlo workload (200,000 seeded
+24 x 24 matrices in one call, against the same matrices one launch each), the
+serving mix (Poisson arrivals, n in 12..40, against FIFO one matrix per
+launch) and the seeded 48 x 48 matrix (all 2^48 Gray indices in bounded
+launches).
 
 With N > 1 (torchrun, one rank per GPU) every rank walks its 1/N share of each
 matrix's Gray range (Sec. 3.1's block split) and the two 64-bit counts are
@@ -367,7 +370,9 @@ def run_ours(args):
             from paper_2407_20205_gb300 import serve
             out, _, _ = serve.run(jobs=args.serve_jobs, nmin=12, nmax=40, rho=0.7, capacity=value)
             extra["serve"] = out
-        if args.long and world == 1:
+        if not args.no_config1 and world == 1:
+            extra["config1_n20"] = bench_n20(pf3, torch, dev, stream)
+        if not args.no_long and world == 1:
             extra["long_n48"] = bench_long(pf3)
         cpu = None
         if not args.no_cpu_baseline and world == 1:
@@ -443,15 +448,53 @@ def bench_single_launches(pf3, torch, dev, stream, count=2000):
             "subsets_per_s": count * (1 << 24) / (ms * 1e-3)}
 
 
+def alu_peak_ops(pf3):
+    """ALU-pipe lane-instructions per second of the whole GPU at the measured
+    maximum SM clock (64 lanes per clock per SM)."""
+    n_sm = pf3.device_info()["sm_count"]
+    return n_sm * float(peaks().get("sm_max_mhz", 2070.0)) * 1e6 * 64
+
+
+def bench_n20(pf3, torch, dev, stream, launches=200):
+    """The seeded uniform 20 x 20 matrix: all 2^20 Gray indices, one matrix per
+    launch, timed over `launches` back-to-back launches with CUDA events on
+    the launching stream (a launch this short is bound by its fixed costs)."""
+    from paper_2407_20205_gb300 import inputs
+    A = inputs.uniform_matrix(inputs.SEED_N20, 20)
+    dA = torch.from_numpy(A).to(dev)
+    out = torch.zeros(3, dtype=torch.int64, device=dev)
+    last = (1 << 20) - 1
+    with torch.cuda.stream(stream):
+        for _ in range(5):
+            pf3.perm_f3_range_counts_async(dA, 20, 0, last, out, stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(launches):
+            pf3.perm_f3_range_counts_async(dA, 20, 0, last, out, stream)
+        e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1) / launches
+    g = pf3.variant_info(pf3.SINGLE, pf3.get_variant(pf3.SINGLE_SHORT, 1))["G"]
+    sub_s = (1 << 20) / (ms * 1e-3)
+    p, m, r = [int(x) % (1 << 64) for x in out.cpu()]
+    return {"n": 20, "launches": launches, "ms_per_launch": ms, "subsets_per_s": sub_s, "perms_per_s": 1e3 / ms,
+            "perm": r, "alu_frac": sub_s * i_alg(g) / alu_peak_ops(pf3), "alu_ops_per_subset": i_alg(g)}
+
+
 def bench_long(pf3):
-    """48 x 48 seeded uniform matrix, all 2^48 Gray indices in bounded launches."""
+    """48 x 48 seeded uniform matrix, all 2^48 Gray indices in bounded launches
+    of 2^44 (16 launches, each followed by a host read of its counts)."""
     from paper_2407_20205_gb300 import inputs
     A = inputs.uniform_matrix(inputs.SEED_N48, 48)
     t0 = time.perf_counter()
     r = pf3.longrun(A, chunk_log2=44)
     dt = time.perf_counter() - t0
-    return {"n": 48, "seconds": dt, "subsets_per_s": (1 << 48) / dt, "perm": r.get("perm"),
-            "plus": r["plus"], "minus": r["minus"], "launches": 1 << 4}
+    g = pf3.variant_info(pf3.SINGLE, pf3.get_variant(pf3.SINGLE, 2))["G"]
+    sub_s = (1 << 48) / dt
+    return {"n": 48, "seconds": dt, "subsets_per_s": sub_s, "perm": r.get("perm"),
+            "plus": r["plus"], "minus": r["minus"], "launches": 1 << 4,
+            "alu_frac": sub_s * i_alg(g) / alu_peak_ops(pf3), "alu_ops_per_subset": i_alg(g),
+            "timing": "host wall clock around pf3_longrun (includes 16 synchronising count reads)"}
 
 
 def main():
@@ -463,8 +506,9 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--serve-jobs", type=int, default=600)
-    ap.add_argument("--long", action="store_true", help="also walk the seeded 48x48 matrix (about a minute)")
+    ap.add_argument("--serve-jobs", type=int, default=5000)
+    ap.add_argument("--no-config1", action="store_true", help="skip the seeded 20x20 matrix")
+    ap.add_argument("--no-long", action="store_true", help="skip the seeded 48x48 matrix (about 40 s)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

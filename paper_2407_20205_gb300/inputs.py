@@ -242,3 +242,31 @@ def poisson_arrivals(seed: int, count: int, rate_per_s: float) -> np.ndarray:
         t += -np.log1p(-u) / rate_per_s
         out[i] = t
     return out
+
+
+def pooled_columns(seed: int, n: int, low_pool: int, high_pool: int | None) -> np.ndarray:
+    """An n x n matrix whose columns 0..31 are each a random nonzero multiple
+    (1 or 2) of one of `low_pool` random column vectors, and whose columns
+    32..n-1 are drawn the same way from `high_pool` vectors (uniform entries
+    when high_pool is None).  A row subset's column sums then take few
+    distinct values on each 32-column word, so the share of subsets whose
+    first 32 sums are all nonzero is about (2/3)^low_pool instead of
+    (2/3)^32: a small pool makes most subsets pass that test.  Drawn from the
+    splitmix64 stream (seed, 0)."""
+    st = Stream(seed, 0)
+    A = np.zeros((n, n), dtype=np.uint8)
+
+    def fill(cols, pool):
+        if not cols:
+            return
+        if pool is None:
+            A[:, cols] = uniform_matrix_from_stream(st, n)[:, :len(cols)]
+            return
+        vecs = uniform_matrix_from_stream(st, max(n, pool))[:pool, :n]
+        for c in cols:
+            k = st.below(pool)
+            A[:, c] = (vecs[k].astype(np.int64) * (1 + st.below(2)) % 3).astype(np.uint8)
+
+    fill(list(range(min(32, n))), low_pool)
+    fill(list(range(32, n)), high_pool)
+    return A

@@ -268,6 +268,17 @@ def test_config_sizes_sampled_ranges(pf3, oracle, n):
         assert pf3.perm_f3_range_counts(A, a, b) == oracle.ryser_range_par(At, a, b)
 
 
+def test_config_n48_window_with_nonzero_terms(pf3, oracle):
+    """The seeded 48 x 48 matrix: a ragged window of 2^31 Gray indices, count
+    for count, with the nonzero terms it must hold (about 7.5 expected)."""
+    A = inputs.uniform_matrix(inputs.SEED_N48, 48)
+    a = (1 << 40) + 99
+    b = a + (1 << 31) + 17
+    want = oracle.ryser_range_par(T(A), a, b)
+    assert sum(want) >= 5, want
+    assert pf3.perm_f3_range_counts(A, a, b) == want
+
+
 def test_edge_cases(pf3):
     assert pf3.perm_f3(np.zeros((0, 0), np.uint8)) == 1
     assert pf3.perm_f3_counts(np.zeros((0, 0), np.uint8)) == (1, 0)
@@ -492,3 +503,27 @@ def test_autotune_cache_roundtrip(tmp_path):
              " t['tiny_cutoff'], t['items_per_warp'], b.get_variant(2, 1), b.get_variant(2, 2))\n") % root
     second = subprocess.run([sys.executable, "-c", code2], env=env, capture_output=True, text=True, check=True)
     assert second.stdout.split() == first.stdout.split()
+
+
+def test_async_calls_on_different_streams_do_not_race(pf3, oracle):
+    """Two device-pointer calls on two streams and a host-pointer call, issued
+    back to back with no synchronisation between them, share the device's
+    scratch; the library orders them, so each result is the oracle's."""
+    import torch
+    mats = [inputs.uniform_matrix(12000 + k, n) for k, n in enumerate((24, 26, 33))]
+    ranges = [(0, (1 << 24) - 1), (12345, (1 << 26) - 3), (777, 777 + (1 << 28))]
+    want = [oracle.ryser_range_par(T(M), a, b) for M, (a, b) in zip(mats, ranges)]
+    assert all(sum(w) > 0 for w in want)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    dA = [torch.from_numpy(M).cuda() for M in mats[:2]]
+    torch.cuda.synchronize()
+    for rep in range(3):
+        outs = [torch.full((3,), 7 + rep, dtype=torch.int64, device="cuda") for _ in range(2)]
+        torch.cuda.synchronize()
+        pf3.perm_f3_range_counts_async(dA[0], 24, *ranges[0], outs[0], s1)
+        pf3.perm_f3_range_counts_async(dA[1], 26, *ranges[1], outs[1], s2)
+        host = pf3.perm_f3_range_counts(mats[2], *ranges[2])
+        torch.cuda.synchronize()
+        for k in range(2):
+            assert tuple(int(x) for x in outs[k][:2].cpu()) == want[k], (rep, k)
+        assert host == want[2], rep

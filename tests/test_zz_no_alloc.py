@@ -49,6 +49,22 @@ def test_noalloc_matches_allocating_entry_two_calls(env):
     assert got1[2] in (0, 1, 2) and got2[2] in (0, 1, 2)
 
 
+def test_noalloc_matches_oracle_on_a_ragged_window(env, oracle):
+    """Directly against the oracle: a ragged window (neither end on a block
+    boundary) of a two-word matrix that holds nonzero terms."""
+    torch, pf3 = env
+    s = torch.cuda.Stream()
+    A = inputs.uniform_matrix(915, 33)
+    first, last = 54321, 54321 + (1 << 27) + 333
+    want = oracle.ryser_range_par(np.ascontiguousarray(A.T), first, last)
+    assert sum(want) > 0, want
+    dA = torch.from_numpy(A).cuda()
+    out = torch.full((3,), 5, dtype=torch.int64, device="cuda")
+    pf3.perm_f3_range_counts_noalloc(dA, 33, first, last, out, 0, s)
+    s.synchronize()
+    assert tuple(int(x) for x in out[:2].cpu()) == want
+
+
 def test_noalloc_limits_and_bad_entries(env):
     torch, pf3 = env
     s = torch.cuda.Stream()
