@@ -370,6 +370,8 @@ def run_ours(args):
             from paper_2407_20205_gb300 import serve
             out, _, _ = serve.run(jobs=args.serve_jobs, nmin=12, nmax=40, rho=0.7, capacity=value)
             extra["serve"] = out
+        if world == 1:
+            extra["dense_vs_grouped_n39"] = bench_dense(pf3, torch, dev, stream)
         if not args.no_config1 and world == 1:
             extra["config1_n20"] = bench_n20(pf3, torch, dev, stream)
         if not args.no_long and world == 1:
@@ -479,6 +481,30 @@ def bench_n20(pf3, torch, dev, stream, launches=200):
     p, m, r = [int(x) % (1 << 64) for x in out.cpu()]
     return {"n": 20, "launches": launches, "ms_per_launch": ms, "subsets_per_s": sub_s, "perms_per_s": 1e3 / ms,
             "perm": r, "alu_frac": sub_s * i_alg(g) / alu_peak_ops(pf3), "alu_ops_per_subset": i_alg(g)}
+
+
+def bench_dense(pf3, torch, dev, stream, n=39, reps=3):
+    """The dense walk against the grouped walk at one size: J_n (all ones, two
+    thirds of its terms nonzero, every warp in the dense walk) and the seeded
+    uniform n x n matrix, each a full 2^n walk in one launch."""
+    from paper_2407_20205_gb300 import inputs
+    out = torch.zeros(3, dtype=torch.int64, device=dev)
+    res = {}
+    for name, A in (("ones", np.ones((n, n), np.uint8)), ("uniform", inputs.uniform_matrix(3900 + n, n))):
+        dA = torch.from_numpy(A).to(dev)
+        last = (1 << n) - 1
+        with torch.cuda.stream(stream):
+            pf3.perm_f3_range_counts_async(dA, n, 0, last, out, stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                pf3.perm_f3_range_counts_async(dA, n, 0, last, out, stream)
+            e1.record(stream)
+        stream.synchronize()
+        res[name] = {"ms": e0.elapsed_time(e1) / reps, "perm": int(out[2].cpu())}
+    res["n"] = n
+    res["ratio"] = res["ones"]["ms"] / res["uniform"]["ms"]
+    return res
 
 
 def bench_long(pf3):

@@ -370,6 +370,35 @@ __device__ __noinline__ void build_dense_masks(WarpQueue<G>& q, const RowTable<W
     __syncwarp();
 }
 
+// Integer multiply-add, d = a * b + c (low or high 32 bits of the product).
+// On this GPU it issues to the multiply-add pipe, not to the ALU pipe that
+// the bitwise gates saturate; a multiplier the compiler cannot see as a
+// constant keeps it there (a literal 1 would be turned into an ALU add).
+__device__ __forceinline__ uint32_t mad_lo(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
+__device__ __forceinline__ uint32_t mad_hi(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("mad.hi.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
+// 16-byte shared-memory load that the compiler may not move out of a loop:
+// the dense walk reads its 2^G - 1 subset masks from shared memory once per
+// group, and hoisted into registers they would not fit.
+__device__ __forceinline__ uint4 lds128(const uint4* p)
+{
+    uint4 v;
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+    return v;
+}
+
 // Exact walk of Gray blocks [B0, B0 + len) for matrices whose terms are often
 // nonzero (the low-word test would mark most groups, and replaying them one
 // by one costs far more): group K's 2^G states are its base state plus each
@@ -378,44 +407,82 @@ __device__ __noinline__ void build_dense_masks(WarpQueue<G>& q, const RowTable<W
 // is its first index and of an odd group its last, so |S| is even exactly
 // for even K, and consecutive bases differ in row G + tz(K+1), subtracted
 // iff bit tz(K+1)+1 of K+1 is set (the Gray flip at index (K+1)·2^G).
+//
+// Per state the walk computes, for each word, the gate g and the inverted
+// mag word (two LOP3) and tests every column nonzero (one LOP3 writing a
+// predicate).  The sign needs no sgn word: the new sgn is ~(mag ^ sgn ^ g)
+// per word, so the XOR of the new sgn words equals (mag0 ^ sgn0 ^ mag1 ^
+// sgn1) ^ g0 ^ g1 -- a base constant and the two gates, one LOP3 -- and the
+// parity of its popcount is the parity of the number of -1 entries (Sec. 3's
+// poppar).  The (-1)^{|S|} factor, kpar + popcount(s), is folded into the
+// base constant by flipping its bit 0.  The +1 / -1 tallies are kept on the
+// multiply-add pipe: with p the popcount, sum(p) - 2 sum(p >> 1) counts the
+// odd ones, and mad.hi(p, 2^31) is p >> 1; 32-bit tallies are moved into the
+// 64-bit counts every 64 groups (at most 64 x 2^G x 65 < 2^32 per batch).
 template <int W, int G, int U>
 __device__ __noinline__ void walk_dense(const RowTable<W>& tab, const uint4* dk, int n, uint64_t B0, uint64_t len,
                                         Counts* c)
 {
     if (!len) return;
+    const uint32_t one = (uint32_t)(n > 0);  // 1 at run time, opaque to the compiler
+    const uint32_t half = one << 31;
     State<W> base = seed_state<W>(tab, n, B0 << U);
     const uint64_t K_end = (B0 + len) << (U - G);
     unsigned long long plus = 0, minus = 0;
-    for (uint64_t K = B0 << (U - G);;) {
-        const uint32_t kpar = (uint32_t)K & 1u;
-        if (all_ones<W>(base)) {
-            uint32_t par = kpar;
-#pragma unroll
-            for (int w = 0; w < W; ++w) par += __popc(base.s[w]);
-            if (par & 1u) ++minus;
-            else ++plus;
-        }
-#pragma unroll 7
-        for (int sub = 1; sub < (1 << G); ++sub) {
-            const uint4 k = dk[sub - 1];
-            uint32_t m0 = base.m[0], s0 = base.s[0];
-            add_word(m0, s0, k.x, k.y);
-            bool nz = (m0 == 0xFFFFFFFFu);
-            uint32_t par = kpar + (uint32_t)__popc((unsigned)sub) + (uint32_t)__popc(s0);
+    uint64_t K = B0 << (U - G);
+    bool done = false;
+    while (!done) {
+        uint32_t cnt = 0, sum_p = 0, sum_h = 0;  // nonzero states, sum of p, sum of p >> 1
+        for (int batch = 0; batch < 64; ++batch) {
+            const uint32_t kpar = (uint32_t)K & 1u;
+            uint32_t bw = base.m[0] ^ base.s[0];
+            uint32_t zb = ~base.m[0];
+            uint32_t xb = base.s[0] ^ kpar;
             if (W > 1) {
-                uint32_t m1 = base.m[W - 1], s1 = base.s[W - 1];
-                add_word(m1, s1, k.z, k.w);
-                nz = nz && (m1 == 0xFFFFFFFFu);
-                par += (uint32_t)__popc(s1);
+                bw ^= base.m[W - 1] ^ base.s[W - 1];
+                zb |= ~base.m[W - 1];
+                xb ^= base.s[W - 1];
             }
-            if (nz) {
-                if (par & 1u) ++minus;
-                else ++plus;
+            const uint32_t be = bw ^ kpar, bo = be ^ 1u;
+            {
+                // the base state itself (s = {})
+                const uint32_t p = __popc(xb);
+                if (zb == 0u) {
+                    cnt = mad_lo(one, one, cnt);
+                    sum_p = mad_lo(p, one, sum_p);
+                    sum_h = mad_hi(p, half, sum_h);
+                }
             }
+#pragma unroll
+            for (int sub = 1; sub < (1 << G); ++sub) {
+                const uint4 k = lds128(dk + (sub - 1));
+                const uint32_t g0 = lop3<kLutG>(base.s[0], k.x, k.y);
+                const uint32_t z0 = lop3<kLutMagInv>(base.m[0], k.x, g0);
+                uint32_t z = z0, x;
+                if (W > 1) {
+                    const uint32_t g1 = lop3<kLutG>(base.s[W - 1], k.z, k.w);
+                    z |= lop3<kLutMagInv>(base.m[W - 1], k.z, g1);
+                    x = lop3<0x96>((__popc((unsigned)sub) & 1) ? bo : be, g0, g1);  // a ^ b ^ c
+                } else {
+                    x = ((__popc((unsigned)sub) & 1) ? bo : be) ^ g0;
+                }
+                const uint32_t p = __popc(x);
+                if (z == 0u) {
+                    cnt = mad_lo(one, one, cnt);
+                    sum_p = mad_lo(p, one, sum_p);
+                    sum_h = mad_hi(p, half, sum_h);
+                }
+            }
+            if (++K == K_end) {
+                done = true;
+                break;
+            }
+            const int zt = __ffsll((long long)K) - 1;
+            add_row<W>(base, tab, (int)((K >> (zt + 1)) & 1u), G + zt);
         }
-        if (++K == K_end) break;
-        const int z = __ffsll((long long)K) - 1;
-        add_row<W>(base, tab, (int)((K >> (z + 1)) & 1u), G + z);
+        const uint32_t odd = sum_p - 2u * sum_h;
+        minus += odd;
+        plus += cnt - odd;
     }
     c->plus += plus;
     c->minus += minus;

@@ -2,9 +2,12 @@
 
     python -m paper_2407_20205_gb300.profile_case --kind single --n 36
     python -m paper_2407_20205_gb300.profile_case --kind batch --n 24 --count 2000
+    python -m paper_2407_20205_gb300.profile_case --kind ones --n 40
 
 single: perm of the seeded uniform n x n matrix (one launch of the walk);
-batch: one batch call over `count` seeded uniform n x n matrices.
+batch: one batch call over `count` seeded uniform n x n matrices;
+ones: perm of the all-ones matrix J_n (one launch; two thirds of its terms
+are nonzero, so every warp walks it with the dense walk).
 """
 from __future__ import annotations
 
@@ -15,7 +18,7 @@ import numpy as np
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--kind", default="single", choices=["single", "batch"])
+    ap.add_argument("--kind", default="single", choices=["single", "batch", "ones"])
     ap.add_argument("--n", type=int, default=36)
     ap.add_argument("--count", type=int, default=2000)
     ap.add_argument("--seed", type=int, default=None)
@@ -24,6 +27,9 @@ def main():
     if a.kind == "single":
         seed = a.seed if a.seed is not None else a.n
         r = binding.perm_f3(inputs.uniform_matrix(seed, a.n))
+        print(f"perm mod 3 = {r}")
+    elif a.kind == "ones":
+        r = binding.perm_f3(np.ones((a.n, a.n), np.uint8))
         print(f"perm mod 3 = {r}")
     else:
         seed = a.seed if a.seed is not None else inputs.SEED_BATCH24

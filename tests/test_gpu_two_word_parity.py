@@ -117,16 +117,21 @@ ENGINEERED = [
 @pytest.mark.parametrize("n,low_pool,high_pool,regime", ENGINEERED)
 def test_engineered_two_word_windows(pf3, oracle, n, low_pool, high_pool, regime):
     """Windows of 2^22 to 2^26 Gray indices with ragged ends, count for count.
-    In the "replay" mix about a tenth of the probe groups pass the first-word
-    test (below the dense switch: marked groups are queued and replayed
-    exactly, and queues that overflow replay in place); in the "dense" mix
-    nearly all do (the warps switch to the dense walk); the "mixed" one sits
-    near the switch, so some blocks of a warp's share switch and others do
-    not.  In all, the second word fails for most of the states that pass the
-    first."""
+    The regimes hold for kernel variant 0 (probe groups of 2^5 indices,
+    blocks of 2^9: a warp leaves the grouped walk for the dense walk when a
+    block marks at least 129 of its 32 x 16 groups, i.e. about 25 %), which
+    the test pins while it walks: in the "replay" mix about a tenth of the
+    probe groups pass the first-word test (marked groups are queued and
+    replayed exactly, and queues that overflow replay in place); in the
+    "dense" mix nearly all do (the warps switch to the dense walk); the
+    "mixed" one sits near the switch, so some blocks of a warp's share switch
+    and others do not.  In all, the second word fails for most of the states
+    that pass the first.  Every window is walked again with the variant the
+    autotuner chose."""
     A = inputs.pooled_columns(6400 + 10 * n + low_pool, n, low_pool, high_pool)
-    G = pf3.variant_info(pf3.SINGLE, pf3.get_variant(pf3.SINGLE_SHORT, 2))["G"]
-    share = first_word_pass_share(A, G)
+    info = pf3.variant_info(pf3.SINGLE, 0)
+    assert (info["U"], info["G"]) == (9, 5)
+    share = first_word_pass_share(A, info["G"])
     if regime == "replay":
         assert 0.02 < share < 0.15, share
     elif regime == "mixed":
@@ -135,12 +140,24 @@ def test_engineered_two_word_windows(pf3, oracle, n, low_pool, high_pool, regime
         assert share > 0.9, share
     rng = np.random.default_rng(6500 + n + low_pool)
     top = (1 << n) - 1
+    windows = []
     for lg in (22, 24, 26):
         a = int(rng.integers(0, 1 << min(n - 2, 62))) * 3 + 1  # not block aligned
-        b = min(top, a + (1 << lg) + int(rng.integers(1, 1000)))
-        _check_window(pf3, oracle, A, a, b, 50)
+        windows.append((a, min(top, a + (1 << lg) + int(rng.integers(1, 1000))), 50))
     # a window that starts at index 0 (the empty set, a head walked one by one)
-    _check_window(pf3, oracle, A, 0, (1 << 22) + 4321, 20)
+    windows.append((0, (1 << 22) + 4321, 20))
     if n == 64:
         # and one that ends at the last index, 2^64 - 1
-        _check_window(pf3, oracle, A, top - (1 << 23) - 77, top, 20)
+        windows.append((top - (1 << 23) - 77, top, 20))
+    tuned = {c: pf3.get_variant(c, 2) for c in (pf3.SINGLE, pf3.SINGLE_SHORT)}
+    for a, b, at_least in windows:
+        want = oracle.ryser_range_par(T(A), a, b)
+        assert sum(want) >= at_least, (a, b, want)  # the window really holds nonzero terms
+        try:
+            pf3.set_variant(pf3.SINGLE, 2, 0)  # both size classes
+            got0 = pf3.perm_f3_range_counts(A, a, b)
+        finally:
+            pf3.set_variant(pf3.SINGLE, 2, tuned[pf3.SINGLE])
+            pf3.set_variant(pf3.SINGLE_SHORT, 2, tuned[pf3.SINGLE_SHORT])
+        assert got0 == want, (a, b, "variant 0")
+        assert pf3.perm_f3_range_counts(A, a, b) == want, (a, b, "tuned variant")
