@@ -320,6 +320,9 @@ constexpr int kQueueCap = 64;
 // the dense walk: at least 129 of the block's 32 x 2^(U-G) groups marked
 // (a quarter for U - G = 4), where replaying them one by one costs more.
 constexpr unsigned kDenseSwitch = 160;
+// Groups the dense walk evaluates side by side (a divisor of every variant's
+// 2^(U-G) groups per block).
+constexpr int kDenseH = 4;
 
 // A warp's queue slot.  Once a warp switches to the dense walk its queue is
 // empty, so the same bytes hold the dense walk's subset masks: for each
@@ -418,53 +421,72 @@ __device__ __forceinline__ uint4 lds128(const uint4* p)
 // base constant by flipping its bit 0.  The +1 / -1 tallies are kept on the
 // multiply-add pipe: with p the popcount, sum(p) - 2 sum(p >> 1) counts the
 // odd ones, and mad.hi(p, 2^31) is p >> 1; 32-bit tallies are moved into the
-// 64-bit counts every 64 groups (at most 64 x 2^G x 65 < 2^32 per batch).
+// 64-bit counts every 16 batches of kDenseH groups.
 template <int W, int G, int U>
 __device__ __noinline__ void walk_dense(const RowTable<W>& tab, const uint4* dk, int n, uint64_t B0, uint64_t len,
                                         Counts* c)
 {
+    // groups are taken kDenseH at a time: each subset mask is read once and
+    // applied to kDenseH bases held in registers, which gives the schedulers
+    // kDenseH independent chains (the popcount and the shared-memory load
+    // have long latencies) per mask
+    constexpr int H = kDenseH;
+    static_assert(((1 << (U - G)) % H) == 0, "a block holds a whole number of group batches");
     if (!len) return;
     const uint32_t one = (uint32_t)(n > 0);  // 1 at run time, opaque to the compiler
     const uint32_t half = one << 31;
-    State<W> base = seed_state<W>(tab, n, B0 << U);
-    const uint64_t K_end = (B0 + len) << (U - G);
-    unsigned long long plus = 0, minus = 0;
+    State<W> cur = seed_state<W>(tab, n, B0 << U);
     uint64_t K = B0 << (U - G);
-    bool done = false;
-    while (!done) {
-        uint32_t cnt = 0, sum_p = 0, sum_h = 0;  // nonzero states, sum of p, sum of p >> 1
-        for (int batch = 0; batch < 64; ++batch) {
-            const uint32_t kpar = (uint32_t)K & 1u;
-            uint32_t bw = base.m[0] ^ base.s[0];
-            uint32_t zb = ~base.m[0];
-            uint32_t xb = base.s[0] ^ kpar;
-            if (W > 1) {
-                bw ^= base.m[W - 1] ^ base.s[W - 1];
-                zb |= ~base.m[W - 1];
-                xb ^= base.s[W - 1];
-            }
-            const uint32_t be = bw ^ kpar, bo = be ^ 1u;
-            {
-                // the base state itself (s = {})
-                const uint32_t p = __popc(xb);
-                if (zb == 0u) {
-                    cnt = mad_lo(one, one, cnt);
-                    sum_p = mad_lo(p, one, sum_p);
-                    sum_h = mad_hi(p, half, sum_h);
-                }
-            }
+    const uint64_t K_end = (B0 + len) << (U - G);  // K_end - K is a multiple of H
+    unsigned long long plus = 0, minus = 0;
+    uint32_t cnt = 0, sum_p = 0, sum_h = 0;  // nonzero states, sum of p, sum of p >> 1
+    uint32_t batches = 0;
+    for (;;) {
+        State<W> b[H];
+        uint32_t be[H];
+        b[0] = cur;
 #pragma unroll
-            for (int sub = 1; sub < (1 << G); ++sub) {
-                const uint4 k = lds128(dk + (sub - 1));
-                const uint32_t g0 = lop3<kLutG>(base.s[0], k.x, k.y);
-                const uint32_t z0 = lop3<kLutMagInv>(base.m[0], k.x, g0);
-                uint32_t z = z0, x;
+        for (int h = 1; h < H; ++h) {
+            b[h] = b[h - 1];
+            const uint64_t Kh = K + (uint64_t)h;
+            const int zt = __ffsll((long long)Kh) - 1;
+            add_row<W>(b[h], tab, (int)((Kh >> (zt + 1)) & 1u), G + zt);
+        }
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            const uint32_t kpar = (uint32_t)(K + (uint64_t)h) & 1u;
+            uint32_t bw = b[h].m[0] ^ b[h].s[0];
+            uint32_t zb = ~b[h].m[0];
+            uint32_t xb = b[h].s[0] ^ kpar;
+            if (W > 1) {
+                bw ^= b[h].m[W - 1] ^ b[h].s[W - 1];
+                zb |= ~b[h].m[W - 1];
+                xb ^= b[h].s[W - 1];
+            }
+            be[h] = bw ^ kpar;
+            // the base state itself (s = {})
+            const uint32_t p = __popc(xb);
+            if (zb == 0u) {
+                cnt = mad_lo(one, one, cnt);
+                sum_p = mad_lo(p, one, sum_p);
+                sum_h = mad_hi(p, half, sum_h);
+            }
+        }
+#pragma unroll
+        for (int sub = 1; sub < (1 << G); ++sub) {
+            const uint4 k = lds128(dk + (sub - 1));
+#pragma unroll
+            for (int h = 0; h < H; ++h) {
+                const uint32_t g0 = lop3<kLutG>(b[h].s[0], k.x, k.y);
+                uint32_t z = lop3<kLutMagInv>(b[h].m[0], k.x, g0);
+                const uint32_t bsub = (__popc((unsigned)sub) & 1) ? (be[h] ^ 1u) : be[h];
+                uint32_t x;
                 if (W > 1) {
-                    const uint32_t g1 = lop3<kLutG>(base.s[W - 1], k.z, k.w);
-                    z |= lop3<kLutMagInv>(base.m[W - 1], k.z, g1);
-                    x = lop3<0x96>((__popc((unsigned)sub) & 1) ? bo : be, g0, g1);  // a ^ b ^ c
+                    const uint32_t g1 = lop3<kLutG>(b[h].s[W - 1], k.z, k.w);
+                    z |= lop3<kLutMagInv>(b[h].m[W - 1], k.z, g1);
+                    x = lop3<0x96>(bsub, g0, g1);  // a ^ b ^ c
                 } else {
-                    x = ((__popc((unsigned)sub) & 1) ? bo : be) ^ g0;
+                    x = bsub ^ g0;
                 }
                 const uint32_t p = __popc(x);
                 if (z == 0u) {
@@ -473,16 +495,20 @@ __device__ __noinline__ void walk_dense(const RowTable<W>& tab, const uint4* dk,
                     sum_h = mad_hi(p, half, sum_h);
                 }
             }
-            if (++K == K_end) {
-                done = true;
-                break;
-            }
-            const int zt = __ffsll((long long)K) - 1;
-            add_row<W>(base, tab, (int)((K >> (zt + 1)) & 1u), G + zt);
         }
-        const uint32_t odd = sum_p - 2u * sum_h;
-        minus += odd;
-        plus += cnt - odd;
+        K += H;
+        // at most 16 batches x H x 2^G states x 33 in sum_p between flushes
+        if (++batches == 16 || K == K_end) {
+            const uint32_t odd = sum_p - 2u * sum_h;
+            minus += odd;
+            plus += cnt - odd;
+            cnt = sum_p = sum_h = 0;
+            batches = 0;
+        }
+        if (K == K_end) break;
+        cur = b[H - 1];
+        const int zt = __ffsll((long long)K) - 1;
+        add_row<W>(cur, tab, (int)((K >> (zt + 1)) & 1u), G + zt);
     }
     c->plus += plus;
     c->minus += minus;
