@@ -179,19 +179,20 @@ int pf3_count_exhaustive(int n, uint64_t* counts);
 /* A request loop for streams of permanents (the Monte Carlo use of Sec. 4):
  * requests are admitted as device slots free up, each request's Gray range is
  * cut into work items of 2^chunk_log2 indices (Sec. 3.1 blocks), and every
- * launch of the batch kernel runs items of many requests under a work budget
- * (a reserved share for the oldest unfinished request, then least remaining
- * work first).
+ * launch of the batch kernel runs items of many requests under a work budget:
+ * first every request whose remaining work is at most 2^small_work_log2 Gray
+ * indices (least remaining first), then the others in arrival order.
  * Matrices and partial counts stay on the device until a request finishes.
  * A context is driven by its own host thread; all calls are thread-safe. */
 typedef struct pf3_config {
     int32_t max_jobs;        /* device slots (requests resident at once); default 4096 */
     int32_t queue_depth;     /* requests waiting for a slot before PF3_EBUSY; default 2^20 */
-    int32_t chunk_log2;      /* Gray indices per work item (log2); default 20 */
+    int32_t chunk_log2;      /* Gray indices per work item (log2); default 22 */
     int32_t launch_items;    /* work items per launch at most; default 16384 */
     int32_t max_admit;       /* requests admitted per launch at most; default 1024 */
-    int32_t oldest_share;    /* percent of each launch's budget reserved for the oldest
-                                unfinished request before anything else (0..100); default 25 */
+    int32_t small_work_log2; /* requests with at most 2^small_work_log2 Gray indices left
+                                are served first, least remaining first; the others
+                                in arrival order (0..64); default 33 */
     uint64_t launch_budget;  /* Gray indices per launch (soft cap); default 2^33 */
 } pf3_config;
 

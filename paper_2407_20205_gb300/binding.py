@@ -277,7 +277,7 @@ def longrun_cancel(on: bool = True) -> None:
 
 class PF3Config(ctypes.Structure):
     _fields_ = [("max_jobs", ctypes.c_int32), ("queue_depth", ctypes.c_int32), ("chunk_log2", ctypes.c_int32),
-                ("launch_items", ctypes.c_int32), ("max_admit", ctypes.c_int32), ("oldest_share", ctypes.c_int32),
+                ("launch_items", ctypes.c_int32), ("max_admit", ctypes.c_int32), ("small_work_log2", ctypes.c_int32),
                 ("launch_budget", ctypes.c_uint64)]
 
 

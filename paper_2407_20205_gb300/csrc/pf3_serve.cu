@@ -7,9 +7,12 @@
 // the device until its last item finishes.  Each job's Gray range is cut into
 // work items of 2^chunk_log2 indices (Sec. 3.1's blocks of consecutive Gray
 // states).  Every launch of the persistent batch kernel takes items from many
-// jobs at once under a work budget: first a reserved share for the oldest
-// unfinished job (so large jobs always progress), then the jobs with the
-// least remaining work.  Up to two launches are in flight; new requests are
+// jobs at once under a work budget: first every job whose remaining work is
+// small (at most 2^small_work_log2 indices), least remaining first, then the
+// other jobs in arrival order.  Small jobs finish in the next launch, and
+// since they carry a small share of the work the large ones are served much
+// as first-come first-served would serve them, never behind a later large
+// job.  Up to two launches are in flight; new requests are
 // admitted into free slots between launches, so work that arrives while
 // other jobs run overlaps with them on the GPU.  Nothing on the device waits
 // on the host: completion is observed with CUDA events, and the host polls
@@ -213,7 +216,7 @@ bool launch_once(pf3_ctx* x)
             stage_off += nn;
             x->active.push_back(tk);
         }
-        // choose items: the oldest job's reserved share, then least remaining work
+        // choose items: small jobs first, then the others in arrival order
         uint64_t budget = x->cfg.launch_budget;
         int n_items = 0;
         auto issue = [&](int64_t tk, uint64_t share) {
@@ -247,22 +250,28 @@ bool launch_once(pf3_ctx* x)
             }
         };
         if (!x->active.empty()) {
-            // a reserved share for the oldest unfinished request (large
-            // requests always progress), then least remaining work first
-            if (x->cfg.oldest_share > 0) issue(x->active.front(), budget / 100 * (uint64_t)x->cfg.oldest_share);
-            auto remaining = [&](int64_t tk) {
+            // small jobs (remaining work at most 2^small_work_log2), least
+            // remaining first; then the rest in arrival order
+            const int sl = x->cfg.small_work_log2;
+            const uint64_t small = sl >= 64 ? ~0ull : (1ull << sl);
+            auto remaining = [&](int64_t tk) -> uint64_t {
                 const Job& j = x->jobs[tk];
-                return j.nb ? (j.nb - j.cursor) << x->U[j.n <= 32 ? 0 : 1] : (1ull << j.n);
+                if (!j.nb) return 1ull << j.n;
+                const int U = x->U[j.n <= 32 ? 0 : 1];
+                const uint64_t left = j.nb - j.cursor;
+                return (left >> (64 - U)) ? ~0ull : left << U;  // 2^64 (n = 64) saturates
             };
-            std::vector<int64_t> order;
+            std::vector<int64_t> small_jobs, large_jobs;
             for (int64_t tk : x->active)
-                if (x->jobs[tk].items_issued < x->jobs[tk].items_total) order.push_back(tk);
-            std::stable_sort(order.begin(), order.end(),
+                if (x->jobs[tk].items_issued < x->jobs[tk].items_total)
+                    (remaining(tk) <= small ? small_jobs : large_jobs).push_back(tk);
+            std::stable_sort(small_jobs.begin(), small_jobs.end(),
                              [&](int64_t a, int64_t b) { return remaining(a) < remaining(b); });
-            for (int64_t tk : order) {
-                if (budget == 0 || n_items >= x->cfg.launch_items) break;
-                issue(tk, budget);
-            }
+            for (const auto* list : {&small_jobs, &large_jobs})
+                for (int64_t tk : *list) {
+                    if (budget == 0 || n_items >= x->cfg.launch_items) break;
+                    issue(tk, budget);
+                }
             // drop fully issued jobs from the active list
             std::vector<int64_t> keep;
             for (int64_t tk : x->active)
@@ -367,10 +376,10 @@ void pf3_config_default(pf3_config* cfg)
     if (!cfg) return;
     cfg->max_jobs = 4096;
     cfg->queue_depth = 1 << 20;
-    cfg->chunk_log2 = 20;
+    cfg->chunk_log2 = 22;
     cfg->launch_items = 16384;
     cfg->max_admit = 1024;
-    cfg->oldest_share = 25;
+    cfg->small_work_log2 = 33;
     cfg->launch_budget = 1ull << 33;
 }
 
@@ -382,7 +391,7 @@ int pf3_create(pf3_ctx** out, const pf3_config* cfg_in)
     if (cfg_in) cfg = *cfg_in;
     if (cfg.max_jobs < 1 || cfg.max_jobs > (1 << 20) || cfg.queue_depth < 1 || cfg.chunk_log2 < 13 ||
         cfg.chunk_log2 > 62 || cfg.launch_items < 1 || cfg.max_admit < 1 || cfg.launch_budget < 1 ||
-        cfg.oldest_share < 0 || cfg.oldest_share > 100)
+        cfg.small_work_log2 < 0 || cfg.small_work_log2 > 64)
         return PF3_EINVAL;
     int rc;
     DeviceCtx* dc = device_ctx(&rc);

@@ -139,13 +139,14 @@ def main():
     ap.add_argument("--capacity", type=float, default=None,
                     help="subsets/s the offered load is scaled to (default: measured on a 36x36 walk)")
     ap.add_argument("--no-fifo", action="store_true")
-    ap.add_argument("--oldest-share", type=int, default=None, help="percent of each launch for the oldest request")
+    ap.add_argument("--small-work-log2", type=int, default=None,
+                    help="requests with at most 2^k Gray indices left go first (default 33)")
     ap.add_argument("--chunk-log2", type=int, default=None)
     ap.add_argument("--launch-budget-log2", type=int, default=None)
     a = ap.parse_args()
     cfg = {}
-    if a.oldest_share is not None:
-        cfg["oldest_share"] = a.oldest_share
+    if a.small_work_log2 is not None:
+        cfg["small_work_log2"] = a.small_work_log2
     if a.chunk_log2 is not None:
         cfg["chunk_log2"] = a.chunk_log2
     if a.launch_budget_log2 is not None:
