@@ -223,6 +223,10 @@ cudaError_t launch_batch(int W, int v, const BatchArgs& a, int grid, cudaStream_
     return cudaLaunchKernel(fn, dim3(grid), dim3(kBatchThreads), args, 0, stream);
 }
 
+const void* batch_kernel_fn(int W, int v) { return W == 1 ? batch_kernel_ptr<1>(v) : batch_kernel_ptr<2>(v); }
+
+const void* slot_init_fn() { return (const void*)slot_init_kernel; }
+
 cudaError_t launch_slot_init(const SlotInit* inits, int count, const uint8_t* staging, uint8_t* mats,
                              int slot_bytes, unsigned long long* acc, unsigned* left, uint8_t* results,
                              cudaStream_t stream)

@@ -88,6 +88,11 @@ cudaError_t launch_slot_init(const SlotInit* inits, int count, const uint8_t* st
                              int slot_bytes, unsigned long long* acc, unsigned* left, uint8_t* results,
                              cudaStream_t stream);
 int batch_max_ctas_per_sm(int W, int v);
+// the kernels themselves, for graph nodes: variant v of the batch kernel for
+// plane width W (args: one BatchArgs), and the serving slot set-up kernel
+// (args as launch_slot_init's, without the stream; 128 threads per CTA)
+const void* batch_kernel_fn(int W, int v);
+const void* slot_init_fn();
 cudaError_t launch_batch(int W, int v, const BatchArgs& a, int grid, cudaStream_t stream);
 
 }  // namespace pf3

@@ -14,9 +14,11 @@
 // as first-come first-served would serve them, never behind a later large
 // job.  Up to two launches are in flight; new requests are
 // admitted into free slots between launches, so work that arrives while
-// other jobs run overlaps with them on the GPU.  Nothing on the device waits
-// on the host: completion is observed with CUDA events, and the host polls
-// them with short sleeps.
+// other jobs run overlaps with them on the GPU.  Each launch's sequence of
+// copies, kernels and event operations is one CUDA graph per buffer, replayed
+// with that launch's sizes.  Nothing on the device waits on the host:
+// completion is observed with CUDA events, and the host polls them with short
+// sleeps.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -95,6 +97,12 @@ struct pf3_ctx {
     void* h_table[2] = {nullptr, nullptr};
     uint8_t* h_results[2] = {nullptr, nullptr};
     cudaEvent_t ev[2] = {nullptr, nullptr};
+    // One graph per buffer holds a launch's whole sequence; each launch sets
+    // its sizes in the instantiated graph and replays it (see build_graph).
+    cudaGraph_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    cudaGraphNode_t g_stage[2] = {}, g_inits[2] = {}, g_items[2] = {}, g_slot[2] = {};
+    cudaGraphNode_t g_batch[2][2] = {};  // [buffer][class]
     // host bookkeeping
     std::mutex mu;
     std::condition_variable cv_done;
@@ -163,6 +171,85 @@ bool harvest(pf3_ctx* x, bool block)
     x->inflight.pop_front();
     x->cv_done.notify_all();
     return true;
+}
+
+// The launch sequence of buffer b as a graph, one chain of nodes: copies of
+// the staged matrices, the slot set-ups and the work items to the device; the
+// slot set-up kernel; the reset of the item cursors; the batch kernel for
+// n > 32 and the one for n <= 32; then, after the other buffer's previous
+// kernels (event wait), the copy of every slot's result byte to the host.
+// Sizes, grids and item counts change from launch to launch: launch_once
+// sets them in the instantiated graph and disables the nodes a launch does
+// not need (no admissions, no items of a class).
+int build_graph(pf3_ctx* x, int b)
+{
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) return cuda_rc(e);
+    x->graph[b] = g;
+    const size_t inits_bytes = (size_t)x->cfg.max_admit * sizeof(SlotInit);
+    cudaGraphNode_t prev = nullptr;
+    auto dep = [&](cudaGraphNode_t node) { prev = node; };
+    auto copy = [&](cudaGraphNode_t* node, void* dst, const void* src, size_t bytes, cudaMemcpyKind kind) {
+        if (e == cudaSuccess) e = cudaGraphAddMemcpyNode1D(node, g, prev ? &prev : nullptr, prev ? 1 : 0, dst, src,
+                                                          bytes, kind);
+        if (e == cudaSuccess) dep(*node);
+    };
+    copy(&x->g_stage[b], x->d_stage[b], x->h_stage[b], kSlotBytes, cudaMemcpyHostToDevice);
+    copy(&x->g_inits[b], x->d_table[b], x->h_table[b], sizeof(SlotInit), cudaMemcpyHostToDevice);
+    copy(&x->g_items[b], (char*)x->d_table[b] + inits_bytes, (char*)x->h_table[b] + inits_bytes, sizeof(WorkItem),
+         cudaMemcpyHostToDevice);
+    // slot set-up kernel (sizes set per launch)
+    const SlotInit* d_inits = (const SlotInit*)x->d_table[b];
+    int count = 0, slot_bytes = kSlotBytes;
+    const uint8_t* staging = x->d_stage[b];
+    void* sargs[] = {(void*)&d_inits, (void*)&count, (void*)&staging, (void*)&x->d_mats, (void*)&slot_bytes,
+                     (void*)&x->d_acc, (void*)&x->d_left, (void*)&x->d_results};
+    cudaKernelNodeParams kp = {};
+    kp.func = (void*)slot_init_fn();
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(128);
+    kp.kernelParams = sargs;
+    if (e == cudaSuccess) e = cudaGraphAddKernelNode(&x->g_slot[b], g, &prev, 1, &kp);
+    if (e == cudaSuccess) dep(x->g_slot[b]);
+    cudaMemsetParams mp = {};
+    mp.dst = x->d_cursor + 2 * b;
+    mp.value = 0;
+    mp.elementSize = sizeof(unsigned);
+    mp.width = 2;
+    mp.height = 1;
+    cudaGraphNode_t n_cur = nullptr;
+    if (e == cudaSuccess) e = cudaGraphAddMemsetNode(&n_cur, g, &prev, 1, &mp);
+    if (e == cudaSuccess) dep(n_cur);
+    for (int cls = 1; cls >= 0 && e == cudaSuccess; --cls) {
+        BatchArgs a = {};
+        a.As = x->d_mats;
+        a.items = (const WorkItem*)((char*)x->d_table[b] + inits_bytes);
+        a.num_items = 0;
+        a.cursor = x->d_cursor + 2 * b + cls;
+        a.acc = x->d_acc;
+        a.left = x->d_left;
+        a.results = x->d_results;
+        a.hist = nullptr;
+        void* bargs[] = {(void*)&a};
+        cudaKernelNodeParams bp = {};
+        bp.func = (void*)batch_kernel_fn(cls + 1, x->variant[cls]);
+        bp.gridDim = dim3(1);
+        bp.blockDim = dim3(kBatchThreads);
+        bp.kernelParams = bargs;
+        e = cudaGraphAddKernelNode(&x->g_batch[b][cls], g, &prev, 1, &bp);
+        if (e == cudaSuccess) dep(x->g_batch[b][cls]);
+    }
+    // the previous launch (other stream) may still run items of jobs that
+    // finish here: results are copied once its kernels are done too
+    cudaGraphNode_t n_rec = nullptr, n_wait = nullptr, n_res = nullptr;
+    if (e == cudaSuccess) e = cudaGraphAddEventRecordNode(&n_rec, g, &prev, 1, x->kdone[b]);
+    if (e == cudaSuccess) dep(n_rec);
+    if (e == cudaSuccess) e = cudaGraphAddEventWaitNode(&n_wait, g, &prev, 1, x->kdone[b ^ 1]);
+    if (e == cudaSuccess) dep(n_wait);
+    copy(&n_res, x->h_results[b], x->d_results, (size_t)x->cfg.max_jobs, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&x->gexec[b], g, 0);
+    return cuda_rc(e);
 }
 
 // build and enqueue one launch; returns false when there was nothing to do
@@ -285,44 +372,60 @@ bool launch_once(pf3_ctx* x)
     // items: class W = 2 first, then W = 1
     if (n1) std::memcpy(items, cls_items[1].data(), n1 * sizeof(WorkItem));
     if (n0) std::memcpy(items + n1, cls_items[0].data(), n0 * sizeof(WorkItem));
+    // this launch's sizes into buffer buf's graph, then one replay of it
     cudaStream_t s = x->streams[buf];
+    cudaGraphExec_t ge = x->gexec[buf];
     const size_t inits_bytes = (size_t)x->cfg.max_admit * sizeof(SlotInit);
     cudaError_t e = cudaSuccess;
-    if (stage_off) e = cudaMemcpyAsync(x->d_stage[buf], x->h_stage[buf], stage_off, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && n_inits)
-        e = cudaMemcpyAsync(x->d_table[buf], x->h_table[buf], (size_t)n_inits * sizeof(SlotInit),
-                            cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && n0 + n1)
-        e = cudaMemcpyAsync((char*)x->d_table[buf] + inits_bytes, items, (n0 + n1) * sizeof(WorkItem),
-                            cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        e = launch_slot_init((const SlotInit*)x->d_table[buf], n_inits, x->d_stage[buf], x->d_mats, kSlotBytes,
-                             x->d_acc, x->d_left, x->d_results, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(x->d_cursor + 2 * buf, 0, 2 * sizeof(unsigned), s);
+    auto set_copy = [&](cudaGraphNode_t node, void* dst, const void* src, size_t bytes) {
+        if (e == cudaSuccess && bytes) e = cudaGraphExecMemcpyNodeSetParams1D(ge, node, dst, src, bytes,
+                                                                            cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaGraphNodeSetEnabled(ge, node, bytes ? 1u : 0u);
+    };
+    set_copy(x->g_stage[buf], x->d_stage[buf], x->h_stage[buf], stage_off);
+    set_copy(x->g_inits[buf], x->d_table[buf], x->h_table[buf], (size_t)n_inits * sizeof(SlotInit));
+    set_copy(x->g_items[buf], (char*)x->d_table[buf] + inits_bytes, items, (n0 + n1) * sizeof(WorkItem));
+    if (e == cudaSuccess && n_inits) {
+        const SlotInit* d_inits = (const SlotInit*)x->d_table[buf];
+        int count = n_inits, slot_bytes = kSlotBytes;
+        const uint8_t* staging = x->d_stage[buf];
+        void* sargs[] = {(void*)&d_inits, (void*)&count, (void*)&staging, (void*)&x->d_mats, (void*)&slot_bytes,
+                         (void*)&x->d_acc, (void*)&x->d_left, (void*)&x->d_results};
+        cudaKernelNodeParams kp = {};
+        kp.func = (void*)slot_init_fn();
+        kp.gridDim = dim3((unsigned)n_inits);
+        kp.blockDim = dim3(128);
+        kp.kernelParams = sargs;
+        e = cudaGraphExecKernelNodeSetParams(ge, x->g_slot[buf], &kp);
+    }
+    if (e == cudaSuccess) e = cudaGraphNodeSetEnabled(ge, x->g_slot[buf], n_inits ? 1u : 0u);
     const WorkItem* d_items = (const WorkItem*)((char*)x->d_table[buf] + inits_bytes);
     for (int cls = 1; cls >= 0 && e == cudaSuccess; --cls) {
         const size_t cnt = cls == 1 ? n1 : n0;
-        if (!cnt) continue;
-        BatchArgs a;
-        a.As = x->d_mats;
-        a.items = d_items + (cls == 1 ? 0 : n1);
-        a.num_items = (unsigned)cnt;
-        a.cursor = x->d_cursor + 2 * buf + cls;
-        a.acc = x->d_acc;
-        a.left = x->d_left;
-        a.results = x->d_results;
-        a.hist = nullptr;
-        const size_t ctas_needed = (cnt + kBatchThreads / 32 - 1) / (kBatchThreads / 32);
-        int grid = x->grid[cls];
-        if ((size_t)grid > ctas_needed) grid = (int)ctas_needed;
-        e = launch_batch(cls + 1, x->variant[cls], a, grid, s);
+        if (cnt) {
+            BatchArgs a = {};
+            a.As = x->d_mats;
+            a.items = d_items + (cls == 1 ? 0 : n1);
+            a.num_items = (unsigned)cnt;
+            a.cursor = x->d_cursor + 2 * buf + cls;
+            a.acc = x->d_acc;
+            a.left = x->d_left;
+            a.results = x->d_results;
+            a.hist = nullptr;
+            const size_t ctas_needed = (cnt + kBatchThreads / 32 - 1) / (kBatchThreads / 32);
+            int grid = x->grid[cls];
+            if ((size_t)grid > ctas_needed) grid = (int)ctas_needed;
+            void* bargs[] = {(void*)&a};
+            cudaKernelNodeParams bp = {};
+            bp.func = (void*)batch_kernel_fn(cls + 1, x->variant[cls]);
+            bp.gridDim = dim3((unsigned)grid);
+            bp.blockDim = dim3(kBatchThreads);
+            bp.kernelParams = bargs;
+            e = cudaGraphExecKernelNodeSetParams(ge, x->g_batch[buf][cls], &bp);
+        }
+        if (e == cudaSuccess) e = cudaGraphNodeSetEnabled(ge, x->g_batch[buf][cls], cnt ? 1u : 0u);
     }
-    // the previous launch (other stream) may still run items of jobs that
-    // finish here: copy results only after its kernels are done too
-    if (e == cudaSuccess) e = cudaEventRecord(x->kdone[buf], s);
-    if (e == cudaSuccess && x->launches > 0) e = cudaStreamWaitEvent(s, x->kdone[buf ^ 1], 0);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(x->h_results[buf], x->d_results, (size_t)x->cfg.max_jobs, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaGraphLaunch(ge, s);
     if (e == cudaSuccess) e = cudaEventRecord(x->ev[buf], s);
     if (e != cudaSuccess) {
         std::lock_guard<std::mutex> g(x->mu);
@@ -424,11 +527,21 @@ int pf3_create(pf3_ctx** out, const pf3_config* cfg_in)
         ok = ok && cudaEventCreateWithFlags(&x->ev[b], cudaEventDisableTiming) == cudaSuccess;
     }
     ok = ok && cudaMemset(x->d_results, kPending, (size_t)cfg.max_jobs) == cudaSuccess;
+    // both "kernels done" events start recorded (complete), so the first
+    // launch's wait on the other buffer's event is well defined
+    for (int b = 0; b < 2 && ok; ++b) ok = cudaEventRecord(x->kdone[b], x->streams[b]) == cudaSuccess;
     ok = ok && cudaDeviceSynchronize() == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         pf3_destroy(x);
         return PF3_ENOMEM;
+    }
+    for (int b = 0; b < 2; ++b) {
+        if ((rc = build_graph(x, b))) {
+            cudaGetLastError();
+            pf3_destroy(x);
+            return rc;
+        }
     }
     x->free_slots.reserve(cfg.max_jobs);
     for (int sl = cfg.max_jobs - 1; sl >= 0; --sl) x->free_slots.push_back(sl);
@@ -469,6 +582,10 @@ void pf3_destroy(pf3_ctx* x)
         cudaFreeHost(x->h_table[b]);
         cudaFreeHost(x->h_results[b]);
         if (x->ev[b]) cudaEventDestroy(x->ev[b]);
+    }
+    for (int b = 0; b < 2; ++b) {
+        if (x->gexec[b]) cudaGraphExecDestroy(x->gexec[b]);
+        if (x->graph[b]) cudaGraphDestroy(x->graph[b]);
     }
     for (int b = 0; b < 2; ++b) {
         if (x->kdone[b]) cudaEventDestroy(x->kdone[b]);

@@ -108,3 +108,48 @@ def test_cancel_queued(pf3):
         assert ctx.wait(t_big) == pf3.perm_f3(inputs.uniform_matrix(78, 37))
         # the context keeps serving afterwards
         assert ctx.wait(ctx.submit(np.eye(9, dtype=np.uint8))) == 1
+
+
+def test_mix_with_two_word_jobs(pf3, oracle):
+    """The serving mix over its full range n = 12..40, plus two-word jobs that
+    reach the batch kernel's queued replay and dense walks (first 32 columns
+    drawn from a few column vectors) and two-word block-diagonal products
+    with oracle-sized blocks.  Every result in the mix (the batch kernel)
+    equals the single-matrix kernel's alone; every job with n <= 24 equals
+    the oracle's perm; every known-answer job, the two-word block products
+    among them, equals its closed form over oracle-sized factors."""
+    from paper_2407_20205_gb300 import serve
+    trace = serve.make_trace(inputs.SEED_SERVE + 1, 240, 12, 40)
+    extra = []
+    for k, (n, pool) in enumerate([(33, 2), (34, 16), (36, 3), (40, 12), (37, 2), (39, 18)]):
+        extra.append((n, "pooled", inputs.pooled_columns(7700 + k, n, pool, None), None))
+    st = inputs.Stream(7800, 0)
+    for k, n in enumerate((34, 38, 40)):
+        a = n // 2
+        B1, B2 = inputs.uniform_matrix(7810 + k, a), inputs.uniform_matrix(7820 + k, n - a)
+        P1, P2 = inputs.monomial(st, n), inputs.monomial(st, n)
+        M = inputs.f3_matmul(inputs.f3_matmul(P1, inputs.block_diag(B1, B2)), P2)
+        extra.append((n, "blockdiag", M, {"blocks": [B1, B2], "P1": P1, "P2": P2}))
+    # interleave the extra jobs into the trace
+    jobs = []
+    for i, t in enumerate(trace):
+        jobs.append(t)
+        if i % 25 == 0 and extra:
+            jobs.append(extra.pop(0))
+    jobs.extend(extra)
+    assert sum(1 for t in jobs if t[0] > 32) >= 60
+    arrivals = inputs.poisson_arrivals(inputs.SEED_SERVE + 1, len(jobs), 400.0)
+    res, lat, makespan, stats = serve.replay(jobs, arrivals)
+    alone = [pf3.perm_f3(A) for (n, kind, A, parts) in jobs]
+    assert res == alone
+    checked = 0
+    for (n, kind, A, parts), r in zip(jobs, res):
+        ka = known_answer(kind, A, parts, oracle)
+        if ka is not None:
+            assert r == ka, (n, kind)
+            checked += 1
+        elif n <= 24:
+            assert r == oracle.perm_mod3(A), (n, kind)
+            checked += 1
+    assert checked >= 100
+    assert sum(1 for (n, kind, A, parts) in jobs if kind == "blockdiag" and n > 32) >= 3
