@@ -237,21 +237,34 @@ uint64_t pf3_now_ns(void);
 /* ------------------------------------------------------------ bipedal vectors */
 
 /* Elementwise operations on bipedal vectors (Sec. 2, Theorem 2.1): `count`
- * vectors of length n <= 64, vector k given by the host words (m1[k], s1[k])
- * and (m2[k], s2[k]) (column j = bit j); the result (m3[k], s3[k]) is a
- * bipedal representation of the sum, difference, pointwise product or
- * pointwise quotient (quotient: meaningful where the divisor is nonzero).
- * Bits >= n of the results are cleared.  Off the permanent's path. */
+ * vectors of length n.  A vector takes w = ceil(n / 64) host words per plane
+ * (the footnote of Sec. 3 on rows longer than a machine word): vector k is
+ * words k*w .. k*w + w - 1 of m1/s1 (and of m2/s2), column j in bit j % 64 of
+ * its word j / 64.  The result (m3, s3), same layout, is a bipedal
+ * representation of the sum, difference, pointwise product or pointwise
+ * quotient (quotient: meaningful where the divisor is nonzero).  Inputs may
+ * use either representation of 0; bits at and above n are cleared in the
+ * results.  1 <= n <= PF3_VEC_MAX_N and count * w <= PF3_VEC_MAX_WORDS,
+ * else PF3_EINVAL.  Off the permanent's path. */
 #define PF3_OP_ADD 0
 #define PF3_OP_SUB 1
 #define PF3_OP_MUL 2
 #define PF3_OP_DIV 3
+#define PF3_VEC_MAX_N (1 << 24)
+#define PF3_VEC_MAX_WORDS (1LL << 31)
 int pf3_vec_op(int op, int n, int64_t count, const uint64_t* m1, const uint64_t* s1, const uint64_t* m2,
                const uint64_t* s2, uint64_t* m3, uint64_t* s3);
 
-/* psi of Sec. 2: vectors (mag[k], sgn[k]) back to entries {0,1,2} (2 == -1),
- * out: host, count * n bytes, vector k's entries at out[k*n .. k*n + n). */
+/* psi of Sec. 2: vectors (mag, sgn) in the layout above back to entries
+ * {0,1,2} (2 == -1).  out: host, count * n bytes, vector k's entries at
+ * out[k*n .. k*n + n). */
 int pf3_vec_unpack(int n, int64_t count, const uint64_t* mag, const uint64_t* sgn, uint8_t* out);
+
+/* phi of Sec. 2: count vectors of n entries in {0,1,2} (host, count * n
+ * bytes, vector k at in[k*n ..]) to (mag, sgn) in the layout above (host,
+ * count * ceil(n / 64) words each; bits at and above n are 0).  An entry
+ * above 2 gives PF3_EDOMAIN and leaves mag and sgn untouched. */
+int pf3_vec_pack(int n, int64_t count, const uint8_t* in, uint64_t* mag, uint64_t* sgn);
 
 /* ------------------------------------------------------------ diagnostics */
 

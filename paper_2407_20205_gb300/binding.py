@@ -374,9 +374,16 @@ class ServeContext:
 # ------------------------------------------------------------ bipedal vectors
 
 OP_ADD, OP_SUB, OP_MUL, OP_DIV = 0, 1, 2, 3
+VEC_MAX_N = 1 << 24
 _lib_vecop = _sig("pf3_vec_op", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int64, _u64p, _u64p, _u64p,
                                                _u64p, _u64p, _u64p])
 _lib_unpack = _sig("pf3_vec_unpack", ctypes.c_int, [ctypes.c_int, ctypes.c_int64, _u64p, _u64p, _u8p])
+_lib_vpack = _sig("pf3_vec_pack", ctypes.c_int, [ctypes.c_int, ctypes.c_int64, _u8p, _u64p, _u64p])
+
+
+def vec_words(n: int) -> int:
+    """64-bit words per plane of one vector of length n."""
+    return (n + 63) // 64
 
 
 def _u64(a):
@@ -384,12 +391,23 @@ def _u64(a):
     return a, a.ctypes.data_as(_u64p)
 
 
+def _vec_count(n: int, a: np.ndarray) -> int:
+    w = vec_words(n)
+    if a.size % w:
+        raise ValueError(f"a length-{n} vector takes {w} words per plane")
+    return a.size // w
+
+
 def vec_op(op: int, n: int, m1, s1, m2, s2):
-    """Elementwise bipedal add/sub/mul/div of arrays of vectors (Theorem 2.1)."""
+    """Elementwise bipedal add/sub/mul/div of arrays of vectors (Theorem 2.1).
+    Each plane is uint64[count * ceil(n / 64)] (or [count, ceil(n / 64)]);
+    the results have the shape of m1."""
     (m1, p1), (s1, q1), (m2, p2), (s2, q2) = _u64(m1), _u64(s1), _u64(m2), _u64(s2)
-    count = int(m1.shape[0])
-    m3 = np.zeros(count, np.uint64)
-    s3 = np.zeros(count, np.uint64)
+    count = _vec_count(n, m1)
+    if not (m1.size == s1.size == m2.size == s2.size):
+        raise ValueError("planes of different sizes")
+    m3 = np.zeros(m1.shape, np.uint64)
+    s3 = np.zeros(m1.shape, np.uint64)
     _check(_lib_vecop(op, n, count, p1, q1, p2, q2, m3.ctypes.data_as(_u64p), s3.ctypes.data_as(_u64p)),
            "pf3_vec_op")
     return m3, s3
@@ -398,10 +416,23 @@ def vec_op(op: int, n: int, m1, s1, m2, s2):
 def vec_unpack(n: int, mag, sgn) -> np.ndarray:
     """psi: uint8[count, n] entries in {0,1,2}."""
     (m, p), (s, q) = _u64(mag), _u64(sgn)
-    count = int(m.shape[0])
+    count = _vec_count(n, m)
     out = np.zeros((count, n), np.uint8)
     _check(_lib_unpack(n, count, p, q, out.ctypes.data_as(_u8p)), "pf3_vec_unpack")
     return out
+
+
+def vec_pack(X) -> tuple[np.ndarray, np.ndarray]:
+    """phi: uint8[count, n] entries in {0,1,2} to planes uint64[count, ceil(n / 64)]."""
+    x = np.ascontiguousarray(np.asarray(X), dtype=np.uint8)
+    if x.ndim != 2:
+        raise ValueError("[count, n] expected")
+    count, n = x.shape
+    mag = np.zeros((count, vec_words(n)), np.uint64)
+    sgn = np.zeros((count, vec_words(n)), np.uint64)
+    _check(_lib_vpack(n, count, x.ctypes.data_as(_u8p), mag.ctypes.data_as(_u64p), sgn.ctypes.data_as(_u64p)),
+           "pf3_vec_pack")
+    return mag, sgn
 
 
 # ------------------------------------------------------------ diagnostics
@@ -563,5 +594,5 @@ def exported_symbols() -> list[str]:
                         "pf3_count_exhaustive", "pf3_variant_info", "pf3_vec_op",
                         "pf3_vec_unpack", "pf3_set_batch_tuning", "pf3_get_batch_tuning",
                         "pf3_autotune_ex", "pf3_batch_plan", "pf3_variant_threads",
-                        "pf3_range_plan", "pf3_perm_from_counts")
+                        "pf3_range_plan", "pf3_perm_from_counts", "pf3_vec_pack")
             if hasattr(_lib, n)]

@@ -72,3 +72,72 @@ def test_random_vectors_and_psi(pf3):
                   (pf3.OP_MUL, lambda x, y: (x * y) % 3)):
         m3, s3 = pf3.vec_op(op, n, ma, sa, mb, sb)
         assert np.array_equal(pf3.vec_unpack(n, m3, s3), f(A, B).astype(np.uint8))
+
+
+def _enc_words(X, zero_alt=None):
+    """Test-side encoding of rows of X (entries 0..2) into ceil(n/64)-word
+    planes, column j in bit j % 64 of word j // 64; where zero_alt is set,
+    a 0 entry is written as (mag, sgn) = (0, 1)."""
+    count, n = X.shape
+    w = (n + 63) // 64
+    mag = np.zeros((count, w), np.uint64)
+    sgn = np.zeros((count, w), np.uint64)
+    for j in range(n):
+        bit = np.uint64(1) << np.uint64(j % 64)
+        mag[:, j // 64] |= np.where(X[:, j] != 0, bit, np.uint64(0))
+        s = (X[:, j] == 2) if zero_alt is None else ((X[:, j] == 2) | ((X[:, j] == 0) & zero_alt[:, j]))
+        sgn[:, j // 64] |= np.where(s, bit, np.uint64(0))
+    return mag, sgn
+
+
+def _dec_words(mag, sgn, n):
+    count = mag.shape[0]
+    out = np.zeros((count, n), np.int64)
+    for j in range(n):
+        m = (mag[:, j // 64] >> np.uint64(j % 64)) & np.uint64(1)
+        s = (sgn[:, j // 64] >> np.uint64(j % 64)) & np.uint64(1)
+        out[:, j] = np.where(m == 0, 0, np.where(s == 0, 1, 2))
+    return out
+
+
+@pytest.mark.parametrize("n", [65, 128, 200])
+def test_multiword_vectors_against_f3(pf3, n):
+    """Vectors longer than 64 entries, ceil(n/64) words per plane: sum,
+    difference, product and quotient against F3 arithmetic column by column,
+    with inputs that use the (0, 1) zero representation, padding bits cleared
+    in the results, and phi / psi round trips."""
+    rng = np.random.default_rng(n)
+    count = 300
+    A = rng.integers(0, 3, (count, n))
+    B = rng.integers(0, 3, (count, n))
+    ma, sa = _enc_words(A, zero_alt=rng.random((count, n)) < 0.5)
+    mb, sb = _enc_words(B, zero_alt=rng.random((count, n)) < 0.5)
+    w = (n + 63) // 64
+    pad = (~np.uint64(0)) << np.uint64(n % 64) if n % 64 else np.uint64(0)
+    for op, f in ((pf3.OP_ADD, lambda x, y: (x + y) % 3), (pf3.OP_SUB, lambda x, y: (x - y) % 3),
+                  (pf3.OP_MUL, lambda x, y: (x * y) % 3), (pf3.OP_DIV, lambda x, y: (x * y) % 3)):
+        m3, s3 = pf3.vec_op(op, n, ma, sa, mb, sb)
+        assert m3.shape == (count, w)
+        got = _dec_words(m3, s3, n)
+        want = f(A, B)
+        if op == pf3.OP_DIV:
+            keep = B != 0  # the quotient is defined where the divisor is nonzero
+            assert np.array_equal(got[keep], want[keep])
+        else:
+            assert np.array_equal(got, want), op
+        assert not (m3[:, -1] & pad).any() and not (s3[:, -1] & pad).any()
+        assert np.array_equal(pf3.vec_unpack(n, m3, s3), got.astype(np.uint8))
+    pm, ps = pf3.vec_pack(A.astype(np.uint8))
+    assert np.array_equal(pm, _enc_words(A)[0]) and np.array_equal(ps, _enc_words(A)[1])
+    assert np.array_equal(pf3.vec_unpack(n, pm, ps), A.astype(np.uint8))
+
+
+def test_vec_pack_rejects_bad_entries_and_sizes(pf3):
+    X = np.zeros((2, 70), np.uint8)
+    X[1, 66] = 3
+    with pytest.raises(pf3.PF3Error) as e:
+        pf3.vec_pack(X)
+    assert e.value.code == pf3.PF3_EDOMAIN
+    with pytest.raises(ValueError):
+        pf3.vec_op(pf3.OP_ADD, 70, np.zeros(3, np.uint64), np.zeros(3, np.uint64), np.zeros(3, np.uint64),
+                   np.zeros(3, np.uint64))
