@@ -361,13 +361,17 @@ __device__ __noinline__ void queue_drain(WarpQueue<G>& q, const RowTable<W>& tab
     __syncwarp();
 }
 
-// all 32 lanes: the dense walk's subset masks into the warp's queue slot
+// all 32 lanes: the dense walk's subset masks into the warp's queue slot, in
+// Gray order of the subsets
 template <int W, int G>
 __device__ __noinline__ void build_dense_masks(WarpQueue<G>& q, const RowTable<W>& tab, int lane)
 {
+    // entry t - 1 holds subset gray(t) = t ^ (t >> 1), t = 1 .. 2^G - 1: in
+    // this order |s| is odd exactly for odd t
     for (int j = lane; j < (1 << G) - 1; j += 32) {
         uint32_t k1[W], k2[W];
-        subset_masks<W>(tab, (uint64_t)(j + 1), k1, k2);
+        const uint32_t t = (uint32_t)j + 1u;
+        subset_masks<W>(tab, (uint64_t)(t ^ (t >> 1)), k1, k2);
         q.dk[j] = make_uint4(k1[0], k2[0], W > 1 ? k1[W - 1] : 0u, W > 1 ? k2[W - 1] : 0u);
     }
     __syncwarp();
@@ -389,6 +393,36 @@ __device__ __forceinline__ uint32_t mad_hi(uint32_t a, uint32_t b, uint32_t c)
     uint32_t d;
     asm("mad.hi.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
     return d;
+}
+
+// The dense walk's states "base h + the rows of one subset s" for the H bases
+// of a batch, given the subset's masks k (K1, K2 of word 0 and of the last
+// word); ODD = |s| is odd (it flips the sign).  See walk_dense.
+template <int W, int H, bool ODD>
+__device__ __forceinline__ void dense_states(const State<W> (&b)[H], const uint32_t (&be)[H], const uint4 k,
+                                             uint32_t one, uint32_t half, uint32_t& cnt, uint32_t& sum_p,
+                                             uint32_t& sum_h)
+{
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+        const uint32_t g0 = lop3<kLutG>(b[h].s[0], k.x, k.y);
+        uint32_t z = lop3<kLutMagInv>(b[h].m[0], k.x, g0);
+        const uint32_t bsub = ODD ? (be[h] ^ 1u) : be[h];
+        uint32_t x;
+        if (W > 1) {
+            const uint32_t g1 = lop3<kLutG>(b[h].s[W - 1], k.z, k.w);
+            z |= lop3<kLutMagInv>(b[h].m[W - 1], k.z, g1);
+            x = lop3<0x96>(bsub, g0, g1);  // a ^ b ^ c
+        } else {
+            x = bsub ^ g0;
+        }
+        const uint32_t p = __popc(x);
+        if (z == 0u) {
+            cnt = mad_lo(one, one, cnt);
+            sum_p = mad_lo(p, one, sum_p);
+            sum_h = mad_hi(p, half, sum_h);
+        }
+    }
 }
 
 // 16-byte shared-memory load that the compiler may not move out of a loop:
@@ -417,8 +451,9 @@ __device__ __forceinline__ uint4 lds128(const uint4* p)
 // per word, so the XOR of the new sgn words equals (mag0 ^ sgn0 ^ mag1 ^
 // sgn1) ^ g0 ^ g1 -- a base constant and the two gates, one LOP3 -- and the
 // parity of its popcount is the parity of the number of -1 entries (Sec. 3's
-// poppar).  The (-1)^{|S|} factor, kpar + popcount(s), is folded into the
-// base constant by flipping its bit 0.  The +1 / -1 tallies are kept on the
+// poppar).  The (-1)^{|S|} factor, kpar + |s|, is folded into the base
+// constant by flipping its bit 0; the subsets are visited in Gray order, so
+// |s| alternates between odd and even from one to the next.  The +1 / -1 tallies are kept on the
 // multiply-add pipe: with p the popcount, sum(p) - 2 sum(p >> 1) counts the
 // odd ones, and mad.hi(p, 2^31) is p >> 1; 32-bit tallies are moved into the
 // 64-bit counts every 16 batches of kDenseH groups.
@@ -472,30 +507,15 @@ __device__ __noinline__ void walk_dense(const RowTable<W>& tab, const uint4* dk,
                 sum_h = mad_hi(p, half, sum_h);
             }
         }
-#pragma unroll
-        for (int sub = 1; sub < (1 << G); ++sub) {
-            const uint4 k = lds128(dk + (sub - 1));
-#pragma unroll
-            for (int h = 0; h < H; ++h) {
-                const uint32_t g0 = lop3<kLutG>(b[h].s[0], k.x, k.y);
-                uint32_t z = lop3<kLutMagInv>(b[h].m[0], k.x, g0);
-                const uint32_t bsub = (__popc((unsigned)sub) & 1) ? (be[h] ^ 1u) : be[h];
-                uint32_t x;
-                if (W > 1) {
-                    const uint32_t g1 = lop3<kLutG>(b[h].s[W - 1], k.z, k.w);
-                    z |= lop3<kLutMagInv>(b[h].m[W - 1], k.z, g1);
-                    x = lop3<0x96>(bsub, g0, g1);  // a ^ b ^ c
-                } else {
-                    x = bsub ^ g0;
-                }
-                const uint32_t p = __popc(x);
-                if (z == 0u) {
-                    cnt = mad_lo(one, one, cnt);
-                    sum_p = mad_lo(p, one, sum_p);
-                    sum_h = mad_hi(p, half, sum_h);
-                }
-            }
+        // the masks are in Gray order of the subsets (build_dense_masks), so
+        // |s| is odd at odd t: a loop over pairs (t, t + 1) keeps each
+        // sign a compile-time choice with a short loop body
+#pragma unroll 1
+        for (int t = 1; t + 1 < (1 << G); t += 2) {
+            dense_states<W, H, true>(b, be, lds128(dk + (t - 1)), one, half, cnt, sum_p, sum_h);
+            dense_states<W, H, false>(b, be, lds128(dk + t), one, half, cnt, sum_p, sum_h);
         }
+        dense_states<W, H, true>(b, be, lds128(dk + ((1 << G) - 2)), one, half, cnt, sum_p, sum_h);
         K += H;
         // at most 16 batches x H x 2^G states x 33 in sum_p between flushes
         if (++batches == 16 || K == K_end) {
