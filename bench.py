@@ -486,7 +486,9 @@ def bench_n20(pf3, torch, dev, stream, launches=200):
 def bench_dense(pf3, torch, dev, stream, n=39, reps=3):
     """The dense walk against the grouped walk at one size: J_n (all ones, two
     thirds of its terms nonzero, every warp in the dense walk) and the seeded
-    uniform n x n matrix, each a full 2^n walk in one launch."""
+    uniform n x n matrix, each a full 2^n walk in one launch through the
+    device-pointer call (A as it is), and J_n through the host-pointer call,
+    which merges its equal columns first."""
     from paper_2407_20205_gb300 import inputs
     out = torch.zeros(3, dtype=torch.int64, device=dev)
     res = {}
@@ -502,8 +504,19 @@ def bench_dense(pf3, torch, dev, stream, n=39, reps=3):
             e1.record(stream)
         stream.synchronize()
         res[name] = {"ms": e0.elapsed_time(e1) / reps, "perm": int(out[2].cpu())}
+    # the host-pointer call on J_n: its equal columns are merged first (one
+    # plane word instead of two); wall clock around perm_f3, copies included
+    J = np.ones((n, n), np.uint8)
+    pf3.perm_f3(J)
+    t = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        r = pf3.perm_f3(J)
+        t.append((time.perf_counter() - t0) * 1e3)
+    res["ones_merged_host_call"] = {"ms": float(min(t)), "perm": r}
     res["n"] = n
     res["ratio"] = res["ones"]["ms"] / res["uniform"]["ms"]
+    res["ratio_merged"] = res["ones_merged_host_call"]["ms"] / res["uniform"]["ms"]
     return res
 
 

@@ -278,6 +278,21 @@ int pf3_step_table(uint32_t* out);
  * bit j, least significant first.  mag, sgn: host, n uint64 each. */
 int pf3_pack(const uint8_t* A, int n, uint64_t* mag, uint64_t* sgn);
 
+/* The column merge the host-pointer single-matrix calls (perm_f3,
+ * perm_f3_counts, perm_f3_range_counts, pf3_longrun) apply before walking:
+ * columns equal up to a factor -1 are one class; a class of odd multiplicity
+ * is kept once and one of even multiplicity twice (in F3, x^mult is x or x^2),
+ * each as its canonical vector (first nonzero entry 1).  Every Ryser term of
+ * the merged n x m matrix B (n rows, the same row subsets) equals A's times
+ * the product of the factors, (-1)^negate, so the +1/-1 counts are A's,
+ * swapped when negate is 1.  The library merges when n > 32 and m <= 32 (one
+ * plane word instead of two: matrices with many equal columns are those whose
+ * terms are mostly nonzero).  A: host, n*n bytes; B: host, room for n*32
+ * bytes, row-major n x m.  Returns 1 and fills B, m and negate when it merges,
+ * 0 when it does not (nothing written), or a negative code.  Host only; no
+ * device is touched.  (Not in the paper: an exact rewriting of Eq. (2).) */
+int pf3_column_merge(const uint8_t* A, int n, uint8_t* B, int* m, int* negate);
+
 /* Integer-pipe microbenchmark (the roofline denominator of the walk).  kind:
  * 0 LOP3, 1 IMAD, 2 IADD, 3 LOP3+IMAD, 4 full row step (3 LOP3 + compare),
  * 5 POPC, 6 MAX(+IMAD), 7 2 LOP3 + MAX, 8 probe (2 LOP3 + compare),

@@ -437,6 +437,23 @@ def vec_pack(X) -> tuple[np.ndarray, np.ndarray]:
 
 # ------------------------------------------------------------ diagnostics
 
+_lib_colmerge = _sig("pf3_column_merge", ctypes.c_int, [_u8p, ctypes.c_int, _u8p, _ip, _ip])
+
+
+def column_merge(A):
+    """The column merge the host-pointer single-matrix calls apply: (B, negate)
+    with B the n x m matrix walked instead of A, or None when A is walked as
+    it is (host only, no device)."""
+    a, p, n = _square(A)
+    B = np.zeros(n * 32, np.uint8)
+    m, neg = ctypes.c_int(), ctypes.c_int()
+    rc = _check(_lib_colmerge(p, n, B.ctypes.data_as(_u8p), ctypes.byref(m), ctypes.byref(neg)),
+                "pf3_column_merge")
+    if rc == 0:
+        return None
+    return B[:n * m.value].reshape(n, m.value).copy(), bool(neg.value)
+
+
 def step_table() -> np.ndarray:
     """uint32[4, 3, 2, 2]: (mag', sgn') for state, constant c, direction."""
     out = np.zeros(48, dtype=np.uint32)
@@ -594,5 +611,6 @@ def exported_symbols() -> list[str]:
                         "pf3_count_exhaustive", "pf3_variant_info", "pf3_vec_op",
                         "pf3_vec_unpack", "pf3_set_batch_tuning", "pf3_get_batch_tuning",
                         "pf3_autotune_ex", "pf3_batch_plan", "pf3_variant_threads",
-                        "pf3_range_plan", "pf3_perm_from_counts", "pf3_vec_pack")
+                        "pf3_range_plan", "pf3_perm_from_counts", "pf3_vec_pack",
+                        "pf3_column_merge")
             if hasattr(_lib, n)]

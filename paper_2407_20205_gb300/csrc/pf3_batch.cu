@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(kBatchThreads, MINB) batch_kernel(BatchArgs a)
         const int rows = n > U ? n : U;
         for (int r = 0; r < rows; ++r) {
             uint32_t mag[2], sgn[2];
-            pack_row_warp(A, n, r, lane, mag, sgn, bad);
+            pack_row_warp(A, n, n, r, lane, mag, sgn, bad);
             if (lane < W) {
                 uint32_t k1, k2p, k2m;
                 row_masks(mag[lane], sgn[lane], k1, k2p, k2m);

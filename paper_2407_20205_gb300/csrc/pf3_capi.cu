@@ -111,16 +111,68 @@ int check_entries_host(const uint8_t* A, int n)
     return PF3_OK;
 }
 
-// enqueue the single-matrix range walk on `stream` (dA on device)
-int enqueue_range(DeviceCtx* c, const uint8_t* dA, int n, uint64_t first, uint64_t last, unsigned long long* d_out,
-                  cudaStream_t stream)
+// Columns equal up to a factor -1 (2 in F3).  Let column j be l_j times a
+// canonical vector v_c(j) (first nonzero entry 1, l_j = +-1).  For every row
+// subset S the column sum of j is l_j times that of v_c(j), so the product of
+// Eq. (2)'s term is (prod_j l_j) * prod_c (sum over S of v_c)^mult_c, and in
+// F3 x^mult is x for odd mult and x^2 (1 unless x = 0) for even mult: the same
+// as one copy of v_c for odd and two copies for even multiplicity.  Walking
+// the n-row matrix of those columns instead of A changes every term by the
+// one factor prod_j l_j, so the +1/-1 counts are A's, swapped when that
+// factor is -1.  Worth it when the merged matrix fits one plane word and A
+// does not (n > 32, m <= 32): matrices with many equal columns are the ones
+// whose terms are mostly nonzero (the dense walk), where the second word
+// doubles the work per state.
+// On true, B (n rows x m columns, row-major), m and negate describe the merged
+// matrix; on false nothing is written and A is walked as it is.
+bool merge_columns(const uint8_t* A, int n, std::vector<uint8_t>& B, int& m, bool& negate)
 {
-    const int W = n <= 32 ? 1 : 2;
+    if (n <= 32) return false;
+    std::vector<uint8_t> canon((size_t)n * n);  // class vectors, column by column
+    int mult[PF3_MAX_N] = {};
+    int classes = 0;
+    bool neg = false;
+    for (int j = 0; j < n; ++j) {
+        uint8_t v[PF3_MAX_N];
+        int first = -1;
+        for (int i = 0; i < n; ++i)
+            if (A[(size_t)i * n + j] && first < 0) first = i;
+        const bool flip = first >= 0 && A[(size_t)first * n + j] == 2;
+        for (int i = 0; i < n; ++i) {
+            const uint8_t e = A[(size_t)i * n + j];
+            v[i] = flip ? (uint8_t)((3 - e) % 3) : e;  // times 2 = times -1 in F3
+        }
+        neg ^= flip;
+        int k = 0;
+        while (k < classes && std::memcmp(&canon[(size_t)k * n], v, (size_t)n) != 0) ++k;
+        if (k == classes) std::memcpy(&canon[(size_t)classes++ * n], v, (size_t)n);
+        ++mult[k];
+    }
+    int cols = 0;
+    for (int k = 0; k < classes; ++k) cols += (mult[k] & 1) ? 1 : 2;
+    if (cols > 32) return false;
+    B.assign((size_t)n * cols, 0);
+    int col = 0;
+    for (int k = 0; k < classes; ++k)
+        for (int copy = 0; copy < ((mult[k] & 1) ? 1 : 2); ++copy, ++col)
+            for (int i = 0; i < n; ++i) B[(size_t)i * cols + col] = canon[(size_t)k * n + i];
+    m = cols;
+    negate = neg;
+    return true;
+}
+
+// enqueue the single-matrix range walk on `stream` (dA on device: n rows of
+// m columns, m = n unless the columns were merged)
+int enqueue_range(DeviceCtx* c, const uint8_t* dA, int n, int m, uint64_t first, uint64_t last,
+                  unsigned long long* d_out, cudaStream_t stream)
+{
+    const int W = m <= 32 ? 1 : 2;
     const bool is_short = last - first < kShortLaunch - 1;
     const int v = is_short ? c->single_variant_short[W - 1] : c->single_variant[W - 1];
     SingleArgs a;
     std::memset(&a, 0, sizeof(a));
     plan_range(n, first, last, kSingleVariants[v].U, a);
+    a.m = m;
     a.A = dA;
     a.partials = c->d_partials;
     a.ticket = c->d_flags;
@@ -150,21 +202,27 @@ int host_range(const uint8_t* A, int n, uint64_t first, uint64_t last, uint64_t*
     if (rc) return rc;
     if (!A) return PF3_EINVAL;
     if ((rc = check_entries_host(A, n))) return rc;
+    std::vector<uint8_t> B;
+    int m = n;
+    bool negate = false;
+    const bool merged = merge_columns(A, n, B, m, negate);
     DeviceCtx* c = device_ctx(&rc);
     if (!c) return rc;
     std::lock_guard<std::mutex> g(c->mu);
-    const size_t nn = (size_t)n * n;
-    std::memcpy(c->h_A, A, nn);
-    cudaError_t e = cudaMemcpyAsync(c->d_A, c->h_A, nn, cudaMemcpyHostToDevice, c->stream);
+    const size_t bytes = (size_t)n * m;
+    std::memcpy(c->h_A, merged ? B.data() : A, bytes);
+    cudaError_t e = cudaMemcpyAsync(c->d_A, c->h_A, bytes, cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) return cuda_rc(e);
-    if ((rc = enqueue_range(c, c->d_A, n, first, last, c->d_out, c->stream))) return rc;
+    if ((rc = enqueue_range(c, c->d_A, n, m, first, last, c->d_out, c->stream))) return rc;
     e = cudaMemcpyAsync(c->h_out, c->d_out, sizeof(unsigned long long) * 3, cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess) return cuda_rc(e);
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_rc(e);
     if (c->h_out[2] == ~0ull) return PF3_EDOMAIN;
-    if (plus) *plus = c->h_out[0];
-    if (minus) *minus = c->h_out[1];
-    if (result) *result = (int)c->h_out[2];
+    const unsigned long long P = negate ? c->h_out[1] : c->h_out[0];
+    const unsigned long long M = negate ? c->h_out[0] : c->h_out[1];
+    if (plus) *plus = P;
+    if (minus) *minus = M;
+    if (result) *result = (int)perm_from_counts(n, P, M);
     return PF3_OK;
 }
 
@@ -236,7 +294,22 @@ int perm_f3_range_counts_async(const uint8_t* dA, int n, uint64_t first, uint64_
     DeviceCtx* c = device_ctx(&rc);
     if (!c) return rc;
     std::lock_guard<std::mutex> g(c->mu);
-    return enqueue_range(c, dA, n, first, last, (unsigned long long*)d_out, (cudaStream_t)stream);
+    return enqueue_range(c, dA, n, n, first, last, (unsigned long long*)d_out, (cudaStream_t)stream);
+}
+
+int pf3_column_merge(const uint8_t* A, int n, uint8_t* B, int* m, int* negate)
+{
+    if (!A || !B || !m || !negate || n < 1 || n > PF3_MAX_N) return PF3_EINVAL;
+    int rc = check_entries_host(A, n);
+    if (rc) return rc;
+    std::vector<uint8_t> buf;
+    int mm = n;
+    bool neg = false;
+    if (!merge_columns(A, n, buf, mm, neg)) return 0;  // nothing written
+    std::memcpy(B, buf.data(), buf.size());
+    *m = mm;
+    *negate = neg ? 1 : 0;
+    return 1;
 }
 
 int pf3_step_table(uint32_t* out)

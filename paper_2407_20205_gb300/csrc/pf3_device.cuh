@@ -6,7 +6,10 @@
 // the paper's appendix packs most significant first, which only permutes the
 // columns and leaves the permanent unchanged).  phi: 0 -> (0,0), 1 -> (1,0),
 // -1 -> (1,1); (0,1) is a second representation of 0 (Definition 2.1).
-// Each plane is held as W 32-bit words (W = 1 for n <= 32, 2 for n <= 64).
+// Each plane is held as W 32-bit words (W = 1 for up to 32 columns, 2 for up
+// to 64).  The walk functions below take the number of columns as `n`: it only
+// places the padding; the rows come from the row table (a matrix of n rows
+// may be walked with fewer columns, see pf3_capi.cu's column merge).
 //
 // Row step (Sec. 2, Theorem 2.1 and the addition truth table, Table 1):
 // adding a row r, or subtracting it, adds a per-column constant c in F3 to the
@@ -636,33 +639,35 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v)
 
 namespace pf3 {
 
-// Pack row r of the n x n matrix A (entries {0,1,2}, 2 == -1) into bit planes
-// with one warp: lane l reads column l (and 32 + l).  Implements phi of Sec. 2
-// column by column.  `bad` is set in the lanes that saw an entry above 2.
-__device__ __forceinline__ void pack_row_warp(const uint8_t* A, int n, int r, int lane, uint32_t (&mag)[2],
-                                              uint32_t (&sgn)[2], bool& bad)
+// Pack row r of the rows x cols matrix A (row-major, entries {0,1,2}, 2 == -1)
+// into bit planes with one warp: lane l reads column l (and 32 + l).
+// Implements phi of Sec. 2 column by column.  `bad` is set in the lanes that
+// saw an entry above 2.
+__device__ __forceinline__ void pack_row_warp(const uint8_t* A, int rows, int cols, int r, int lane,
+                                              uint32_t (&mag)[2], uint32_t (&sgn)[2], bool& bad)
 {
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int col = 32 * h + lane;
         uint32_t a = 0;
-        if (r < n && col < n) a = A[(size_t)r * n + col];
+        if (r < rows && col < cols) a = A[(size_t)r * cols + col];
         bad |= (a > 2u);
         mag[h] = __ballot_sync(0xFFFFFFFFu, a == 1u || a == 2u);
         sgn[h] = __ballot_sync(0xFFFFFFFFu, a == 2u);
     }
 }
 
-// Build the row table of A with the warps [warp0, warp0 + nwarps) of the
-// calling group; every row r >= n is the identity (adds 0).
+// Build the row table of the rows x cols matrix A with the warps
+// [warp0, warp0 + nwarps) of the calling group; every row r >= rows is the
+// identity (adds 0).
 template <int W>
-__device__ __forceinline__ bool build_row_table(RowTable<W>& tab, const uint8_t* A, int n, int warp, int nwarps,
-                                                int lane)
+__device__ __forceinline__ bool build_row_table(RowTable<W>& tab, const uint8_t* A, int rows, int cols, int warp,
+                                                int nwarps, int lane)
 {
     bool bad = false;
     for (int r = warp; r < kMaxN; r += nwarps) {
         uint32_t mag[2], sgn[2];
-        pack_row_warp(A, n, r, lane, mag, sgn, bad);
+        pack_row_warp(A, rows, cols, r, lane, mag, sgn, bad);
         if (lane < W) {
             uint32_t k1, k2p, k2m;
             row_masks(mag[lane], sgn[lane], k1, k2p, k2m);

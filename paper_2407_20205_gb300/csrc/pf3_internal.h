@@ -44,8 +44,9 @@ static_assert(kNumSingleVariants <= kMaxVariants && kNumBatchVariants <= kMaxVar
 
 // One range job for the single-matrix kernel; all indices are Gray indices.
 struct SingleArgs {
-    const uint8_t* A;        // device, n*n row-major {0,1,2}
-    int n;
+    const uint8_t* A;        // device, n rows x m columns, row-major {0,1,2}
+    int n;                   // rows: the Gray range is [0, 2^n) and the sign (-1)^n
+    int m;                   // columns (n unless the host merged equal columns)
     int has_head;            // generic walk of [head_first, head_last]
     int has_tail;            // generic walk of [tail_first, tail_last]
     uint64_t head_first, head_last;
@@ -97,14 +98,14 @@ __host__ __device__ inline void chunk_range(const SingleArgs& a, unsigned k, uin
 }
 
 // split [first, last] into a ragged head, aligned middle blocks of 2^U
-// indices and a ragged tail
+// indices and a ragged tail (sets a.n = a.m = n)
 void plan_range(int n, uint64_t first, uint64_t last, int U, SingleArgs& a);
 
 // split the middle blocks into the chunks warps take from the cursor, for
 // `grid` CTAs of `threads` threads
 void plan_chunks(SingleArgs& a, int grid, int threads);
 
-// launch variant `v` of the single-matrix walk (W = 1 for n <= 32, else 2);
+// launch variant `v` of the single-matrix walk (W = 1 for m <= 32 columns, else 2);
 // plans the chunks for `grid` CTAs
 cudaError_t launch_single(const SingleArgs& a, int v, int grid, cudaStream_t stream);
 

@@ -18,14 +18,16 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "perm_f3.h"
 #include "pf3_context.h"
 #include "pf3_internal.h"
 
 namespace pf3 {
-int enqueue_range(DeviceCtx* c, const uint8_t* dA, int n, uint64_t first, uint64_t last, unsigned long long* d_out,
-                  cudaStream_t stream);
+int enqueue_range(DeviceCtx* c, const uint8_t* dA, int n, int m, uint64_t first, uint64_t last,
+                  unsigned long long* d_out, cudaStream_t stream);
+bool merge_columns(const uint8_t* A, int n, std::vector<uint8_t>& B, int& m, bool& negate);
 }
 
 using namespace pf3;
@@ -111,7 +113,12 @@ int pf3_longrun(const uint8_t* A, int n, int chunk_log2, const char* checkpoint_
     const uint64_t last = (n == 64) ? ~0ull : ((1ull << n) - 1);
     const uint64_t step_m1 = (1ull << chunk_log2) - 1;
     const auto t0 = std::chrono::steady_clock::now();
-    const size_t nn = (size_t)n * n;
+    // equal columns merged as for perm_f3 (pf3_capi.cu); the counts are A's
+    std::vector<uint8_t> B;
+    int m = n;
+    bool negate = false;
+    const uint8_t* src = merge_columns(A, n, B, m, negate) ? B.data() : A;
+    const size_t bytes = (size_t)n * m;
     while (!rc && !ck.done) {
         if (g_cancel.load()) {
             rc = PF3_ECANCELED;
@@ -124,16 +131,16 @@ int pf3_longrun(const uint8_t* A, int n, int chunk_log2, const char* checkpoint_
             // calls on this device interleave with a long walk; the matrix is
             // copied again each time because they share the staging buffers
             std::lock_guard<std::mutex> g(c->mu);
-            std::memcpy(c->h_A, A, nn);
-            cudaError_t e = cudaMemcpyAsync(c->d_A, c->h_A, nn, cudaMemcpyHostToDevice, c->stream);
+            std::memcpy(c->h_A, src, bytes);
+            cudaError_t e = cudaMemcpyAsync(c->d_A, c->h_A, bytes, cudaMemcpyHostToDevice, c->stream);
             if ((rc = cuda_rc(e))) break;
-            if ((rc = enqueue_range(c, c->d_A, n, first, stop, c->d_out, c->stream))) break;
+            if ((rc = enqueue_range(c, c->d_A, n, m, first, stop, c->d_out, c->stream))) break;
             e = cudaMemcpyAsync(c->h_out, c->d_out, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                                 c->stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
             if ((rc = cuda_rc(e))) break;
-            ck.plus += c->h_out[0];
-            ck.minus += c->h_out[1];
+            ck.plus += negate ? c->h_out[1] : c->h_out[0];
+            ck.minus += negate ? c->h_out[0] : c->h_out[1];
         }
         if (stop == last) ck.done = 1;
         else ck.cursor = stop + 1;

@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(THREADS, MINB) single_kernel(SingleArgs a)
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     if (lane == 0) queues[warp].count = 0;
-    const bool bad_local = build_row_table<W>(tab, a.A, a.n, warp, THREADS / 32, lane);
+    const bool bad_local = build_row_table<W>(tab, a.A, a.n, a.m, warp, THREADS / 32, lane);
     const bool bad = __syncthreads_or(bad_local) != 0;
 
     Counts c{0ull, 0ull};
@@ -50,8 +50,8 @@ __global__ void __launch_bounds__(THREADS, MINB) single_kernel(SingleArgs a)
                 split_range(a.mid_NB, T, tid, s, len);
                 const uint64_t trip = __shfl_sync(0xFFFFFFFFu, len, 0);  // lane 0 holds the longest share
                 const uint64_t done =
-                    walk_groups<W, G, U>(tab, R, a.n, a.mid_B0 + s, len, trip, queues[warp], lane, c);
-                if (done < len) walk_dense<W, G, U>(tab, queues[warp].dk, a.n, a.mid_B0 + s + done, len - done, &c);
+                    walk_groups<W, G, U>(tab, R, a.m, a.mid_B0 + s, len, trip, queues[warp], lane, c);
+                if (done < len) walk_dense<W, G, U>(tab, queues[warp].dk, a.m, a.mid_B0 + s + done, len - done, &c);
             } else {
                 // the cursor only grows, and every chunk index at or past
                 // nchunks ends the loop: at most nchunks + 1 turns per warp
@@ -65,14 +65,14 @@ __global__ void __launch_bounds__(THREADS, MINB) single_kernel(SingleArgs a)
                     split_range(clen, 32, (uint64_t)lane, s, len);
                     const uint64_t trip = __shfl_sync(0xFFFFFFFFu, len, 0);
                     const uint64_t done =
-                        walk_groups<W, G, U>(tab, R, a.n, a.mid_B0 + cs + s, len, trip, queues[warp], lane, c);
+                        walk_groups<W, G, U>(tab, R, a.m, a.mid_B0 + cs + s, len, trip, queues[warp], lane, c);
                     if (done < len)
-                        walk_dense<W, G, U>(tab, queues[warp].dk, a.n, a.mid_B0 + cs + s + done, len - done, &c);
+                        walk_dense<W, G, U>(tab, queues[warp].dk, a.m, a.mid_B0 + cs + s + done, len - done, &c);
                 }
             }
         }
-        if (a.has_head && tid == T - 1) walk_generic<W>(tab, a.n, a.head_first, a.head_last, c);
-        if (a.has_tail && tid == (T > 1 ? T - 2 : 0)) walk_generic<W>(tab, a.n, a.tail_first, a.tail_last, c);
+        if (a.has_head && tid == T - 1) walk_generic<W>(tab, a.m, a.head_first, a.head_last, c);
+        if (a.has_tail && tid == (T > 1 ? T - 2 : 0)) walk_generic<W>(tab, a.m, a.tail_first, a.tail_last, c);
     }
 
     unsigned long long p = warp_sum(c.plus);
@@ -163,7 +163,7 @@ __global__ void pack_kernel(const uint8_t* A, int n, unsigned long long* out_mag
     bool bad = false;
     for (int r = warp; r < n; r += blockDim.x / 32) {
         uint32_t mag[2], sgn[2];
-        pack_row_warp(A, n, r, lane, mag, sgn, bad);
+        pack_row_warp(A, n, n, r, lane, mag, sgn, bad);
         if (lane == 0) {
             out_mag[r] = ((unsigned long long)mag[1] << 32) | mag[0];
             out_sgn[r] = ((unsigned long long)sgn[1] << 32) | sgn[0];
@@ -202,6 +202,7 @@ const void* single_kernel_ptr(int v)
 void plan_range(int n, uint64_t first, uint64_t last, int U, SingleArgs& a)
 {
     a.n = n;
+    a.m = n;
     a.has_head = a.has_tail = 0;
     a.mid_B0 = a.mid_NB = 0;
     a.head_first = a.head_last = a.tail_first = a.tail_last = 0;
@@ -287,7 +288,7 @@ cudaError_t launch_single(const SingleArgs& args, int v, int grid, cudaStream_t 
     SingleArgs a = args;
     const int threads = kSingleVariants[v].threads;
     plan_chunks(a, grid, threads);
-    const void* fn = a.n <= 32 ? single_kernel_ptr<1>(v) : single_kernel_ptr<2>(v);
+    const void* fn = a.m <= 32 ? single_kernel_ptr<1>(v) : single_kernel_ptr<2>(v);
     void* kargs[] = {(void*)&a};
     return cudaLaunchKernel(fn, dim3(grid), dim3(threads), kargs, 0, stream);
 }

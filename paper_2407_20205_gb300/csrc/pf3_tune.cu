@@ -25,8 +25,8 @@
 
 namespace pf3 {
 
-int enqueue_range(DeviceCtx* c, const uint8_t* dA, int n, uint64_t first, uint64_t last, unsigned long long* d_out,
-                  cudaStream_t stream);
+int enqueue_range(DeviceCtx* c, const uint8_t* dA, int n, int m, uint64_t first, uint64_t last,
+                  unsigned long long* d_out, cudaStream_t stream);
 
 namespace {
 
@@ -291,7 +291,7 @@ int pf3_autotune_ex(double* single_ms, double* single_short_ms, double* batch_ms
         for (int v = 0; v < kNumSingleVariants; ++v) {
             c->single_variant[W - 1] = v;
             const float ms = time_ms(s, 2, [&] {
-                enqueue_range(c, dA, n, 0, (1ull << lgW[W - 1]) - 1, dout, s);
+                enqueue_range(c, dA, n, n, 0, (1ull << lgW[W - 1]) - 1, dout, s);
             });
             if (single_ms) single_ms[(W - 1) * kNumSingleVariants + v] = ms;
             if (v == 0 || ms < kVariantMargin * best) {
@@ -315,7 +315,7 @@ int pf3_autotune_ex(double* single_ms, double* single_short_ms, double* batch_ms
         for (int v = 0; v < kNumSingleVariants; ++v) {
             c->single_variant_short[W - 1] = v;
             const float ms = time_ms(s, 20, [&] {
-                enqueue_range(c, dA, n, 0, (1ull << lgS[W - 1]) - 1, dout, s);
+                enqueue_range(c, dA, n, n, 0, (1ull << lgS[W - 1]) - 1, dout, s);
             });
             if (single_short_ms) single_short_ms[(W - 1) * kNumSingleVariants + v] = ms;
             if (v == 0 || ms < kVariantMargin * best) {

@@ -175,15 +175,35 @@ def _rank_one(seed, n):
     return A.astype(np.uint8), d, e
 
 
+def _device_counts(pf3, A):
+    """Counts over all 2^n indices through the device-pointer path, which
+    walks A as it is (the host-pointer calls may merge equal columns)."""
+    import torch
+    n = A.shape[0]
+    dA = torch.from_numpy(np.ascontiguousarray(A)).cuda()
+    out = torch.zeros(3, dtype=torch.int64, device="cuda")
+    pf3.perm_f3_range_counts_async(dA, n, 0, (1 << n) - 1, out, None)
+    torch.cuda.synchronize()
+    return tuple(int(x) % (1 << 64) for x in out[:2].cpu())
+
+
 @pytest.mark.parametrize("n", [14, 20, 27, 33, 36, 40])
 def test_dense_terms_closed_form(pf3, n):
     """Matrices with 2/3 of their terms nonzero (all columns proportional)
     send every warp into the dense walk: the exact counts must equal the
-    closed form, for J_n and for D1 J D2 with random signs."""
+    closed form, for J_n and for D1 J D2 with random signs -- through the
+    device-pointer path (A as it is: two plane words for n > 32) and the
+    host-pointer one (for n > 32 the columns merge into one or two)."""
     J = np.ones((n, n), np.uint8)
-    assert pf3.perm_f3_counts(J) == rank_one_counts([1] * n, [1] * n)
+    want = rank_one_counts([1] * n, [1] * n)
+    assert pf3.perm_f3_counts(J) == want
+    assert _device_counts(pf3, J) == want
     A, d, e = _rank_one(7000 + n, n)
-    assert pf3.perm_f3_counts(A) == rank_one_counts(list(d), list(e))
+    want = rank_one_counts(list(d), list(e))
+    assert pf3.perm_f3_counts(A) == want
+    assert _device_counts(pf3, A) == want
+    if n > 32:
+        assert pf3.column_merge(A) is not None
 
 
 def test_dense_terms_batch_and_ranges(pf3, oracle):

@@ -58,11 +58,23 @@ def first_word_pass_share(A, G, groups=3000, seed=0):
     return float((sums != 0).all(axis=2).any(axis=1).mean())
 
 
+def device_range_counts(pf3, A, a, b):
+    """perm_f3_range_counts_async: the device-pointer path, which walks A as
+    it is (the host-pointer calls may first merge equal columns)."""
+    import torch
+    n = A.shape[0]
+    dA = torch.from_numpy(np.ascontiguousarray(A)).cuda()
+    out = torch.zeros(3, dtype=torch.int64, device="cuda")
+    pf3.perm_f3_range_counts_async(dA, n, a, b, out, None)
+    torch.cuda.synchronize()
+    return tuple(int(x) % (1 << 64) for x in out[:2].cpu())
+
+
 def _check_window(pf3, oracle, A, a, b, at_least):
     want = oracle.ryser_range_par(T(A), a, b)
     assert sum(want) >= at_least, (a, b, want)  # the window really holds nonzero terms
-    got = pf3.perm_f3_range_counts(A, a, b)
-    assert got == want, (a, b)
+    assert pf3.perm_f3_range_counts(A, a, b) == want, (a, b)
+    assert device_range_counts(pf3, A, a, b) == want, (a, b)
 
 
 # ------------------------------------------------------------ the benchmark matrices
@@ -126,8 +138,10 @@ def test_engineered_two_word_windows(pf3, oracle, n, low_pool, high_pool, regime
     "dense" mix nearly all do (the warps switch to the dense walk); the
     "mixed" one sits near the switch, so some blocks of a warp's share switch
     and others do not.  In all, the second word fails for most of the states
-    that pass the first.  Every window is walked again with the variant the
-    autotuner chose."""
+    that pass the first.  The regimes are those of the device-pointer path,
+    which walks A as it is; every window is also walked with the variant the
+    autotuner chose, and through the host-pointer call, which may merge equal
+    columns first."""
     A = inputs.pooled_columns(6400 + 10 * n + low_pool, n, low_pool, high_pool)
     info = pf3.variant_info(pf3.SINGLE, 0)
     assert (info["U"], info["G"]) == (9, 5)
@@ -155,9 +169,11 @@ def test_engineered_two_word_windows(pf3, oracle, n, low_pool, high_pool, regime
         assert sum(want) >= at_least, (a, b, want)  # the window really holds nonzero terms
         try:
             pf3.set_variant(pf3.SINGLE, 2, 0)  # both size classes
-            got0 = pf3.perm_f3_range_counts(A, a, b)
+            got0 = device_range_counts(pf3, A, a, b)
         finally:
             pf3.set_variant(pf3.SINGLE, 2, tuned[pf3.SINGLE])
             pf3.set_variant(pf3.SINGLE_SHORT, 2, tuned[pf3.SINGLE_SHORT])
-        assert got0 == want, (a, b, "variant 0")
-        assert pf3.perm_f3_range_counts(A, a, b) == want, (a, b, "tuned variant")
+        assert got0 == want, (a, b, "variant 0, A as it is")
+        assert device_range_counts(pf3, A, a, b) == want, (a, b, "tuned variant, A as it is")
+        # the host-pointer call (equal columns merged when that fits one plane word)
+        assert pf3.perm_f3_range_counts(A, a, b) == want, (a, b, "host-pointer call")
