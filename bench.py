@@ -388,6 +388,7 @@ def run_ours(args):
                            "parallelism": f"range split x{world}" if world > 1 else "1 GPU",
                            "variants": {"single": tune["single_variant"],
                                         "single_short_launches": tune["single_short_variant"],
+                                        "single_merged_columns": tune["single_merged_variant"],
                                         "batch": tune["batch_variant"]},
                            "batch_tuning": tune["batch_tuning"],
                            "autotune_ms": {"single": tune["single_ms"], "batch": tune["batch_ms"],

@@ -314,9 +314,12 @@ int pf3_device_info(int* sm_count, int* device);
 /* Kernel variants (probe group and unrolled block lengths, register budget,
  * CTA size).  which: 0 = single-matrix kernel, 1 = batch kernel, 2 =
  * single-matrix kernel for launches of fewer than 2^28 Gray indices (their
- * own size class: there the fixed costs of a launch decide).  W: words per
- * plane (1 for n <= 32, 2 for n <= 64).  pf3_set_variant(0, W, v) sets both
- * single-matrix classes; (2, W, v) only the short one; pf3_get_variant(0, W)
+ * own size class: there the fixed costs of a launch decide), 3 = single-matrix
+ * kernel for long launches of a matrix whose equal columns were merged (see
+ * pf3_column_merge; W = 1 only: such matrices have mostly nonzero terms).
+ * W: words per plane (1 for up to 32 columns, 2 for up to 64).
+ * pf3_set_variant(0, W, v) sets both single-matrix size classes; (2, W, v)
+ * only the short one; (3, 1, v) the merged class; pf3_get_variant(0, W)
  * reads the long class.  Results never depend on the variant, only speed
  * does. */
 int pf3_variant_count(int which);
@@ -409,9 +412,10 @@ int pf3_range_plan(int n, uint64_t first, uint64_t last, int variant, int grid, 
 /* Time every variant on the current device and keep the fastest per W (a
  * variant replaces the current choice, variant 0 first, only when it is at
  * least 1 % faster) (single-matrix kernel: n = 32 over 2^31 Gray indices for W = 1, n = 40 over
- * 2^36 for W = 2, and for the short-launch class n = 24 over 2^24 and n = 36
- * over 2^27; batch kernel: 8192 matrices of n = 24 and 32 of n = 33 under the
- * guided split), then pick the batch packing cutoff and split granularity
+ * 2^36 for W = 2, for the short-launch class n = 24 over 2^24 and n = 36
+ * over 2^27, and for the merged class J_36 merged to 36 x 2 over 2^33; batch
+ * kernel: 8192 matrices of n = 24 and 32 of n = 33 under the guided split),
+ * then pick the batch packing cutoff and split granularity
  * (pf3_autotune_ex).
  * single_ms (pf3_variant_count(0) * 2 doubles) and batch_ms
  * (pf3_variant_count(1) * 2 doubles) receive the variant timings, W = 1

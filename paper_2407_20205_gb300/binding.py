@@ -490,7 +490,7 @@ def device_info() -> dict:
 
 # ------------------------------------------------------------ tuning
 
-SINGLE, BATCH, SINGLE_SHORT = 0, 1, 2
+SINGLE, BATCH, SINGLE_SHORT, SINGLE_MERGED = 0, 1, 2, 3
 
 
 def variant_count(which: int) -> int:
@@ -591,6 +591,7 @@ def autotune() -> dict:
     return {"single_ms": {1: list(a)[:ns], 2: list(a)[ns:]},
             "single_short_ms": {1: list(a2)[:ns], 2: list(a2)[ns:]},
             "single_short_variant": {W: get_variant(SINGLE_SHORT, W) for W in (1, 2)},
+            "single_merged_variant": get_variant(SINGLE_MERGED, 1),
             "batch_ms": {1: list(b)[:nb], 2: list(b)[nb:]},
             "pack_ms": {n: [pk[n], pk[TINY_MAX_N + 1 + n]] for n in range(TINY_MAX_N + 1) if pk[n] > 0},
             "split_ms": dict(zip(SPLIT_CANDIDATES, list(sp))),

@@ -168,7 +168,10 @@ int enqueue_range(DeviceCtx* c, const uint8_t* dA, int n, int m, uint64_t first,
 {
     const int W = m <= 32 ? 1 : 2;
     const bool is_short = last - first < kShortLaunch - 1;
-    const int v = is_short ? c->single_variant_short[W - 1] : c->single_variant[W - 1];
+    // m < n only for a merged matrix, whose terms are mostly nonzero (the
+    // dense walk): its long launches take the variant tuned for that
+    const int v = is_short ? c->single_variant_short[W - 1]
+                           : (m < n ? c->single_variant_merged : c->single_variant[W - 1]);
     SingleArgs a;
     std::memset(&a, 0, sizeof(a));
     plan_range(n, first, last, kSingleVariants[v].U, a);

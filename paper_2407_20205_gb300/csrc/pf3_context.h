@@ -55,6 +55,7 @@ struct DeviceCtx {
     int sm_count = 0;
     int single_variant[2] = {0, 0};        // tuned single-kernel variant for W = 1 / W = 2
     int single_variant_short[2] = {0, 0};  // the same for launches of fewer than kShortLaunch indices
+    int single_variant_merged = 0;         // long launches of a matrix with merged columns (one word)
     int single_ctas[2][kMaxVariants] = {};  // resident CTAs per SM by W and variant (0 = not queried)
     int batch_ctas_cache[2][kMaxVariants] = {};
     int max_grid = 0;

@@ -112,15 +112,16 @@ void load_tune_cache(DeviceCtx* c)
     while (std::fgets(line, sizeof(line), f)) {
         std::string l(line);
         if (l.compare(0, key.size(), key) != 0 || l.size() <= key.size() || l[key.size()] != '|') continue;
-        int v[8];
-        const int got = std::sscanf(l.c_str() + key.size() + 1, "%d|%d|%d|%d|%d|%d|%d|%d", &v[0], &v[1], &v[2],
-                                    &v[3], &v[4], &v[5], &v[6], &v[7]);
-        if (got != 4 && got != 6 && got != 8) continue;
+        int v[9];
+        const int got = std::sscanf(l.c_str() + key.size() + 1, "%d|%d|%d|%d|%d|%d|%d|%d|%d", &v[0], &v[1], &v[2],
+                                    &v[3], &v[4], &v[5], &v[6], &v[7], &v[8]);
+        if (got != 4 && got != 6 && got != 8 && got != 9) continue;
         if (v[0] < 0 || v[0] >= kNumSingleVariants || v[1] < 0 || v[1] >= kNumSingleVariants || v[2] < 0 ||
             v[2] >= kNumBatchVariants || v[3] < 0 || v[3] >= kNumBatchVariants)
             continue;
         if (got >= 6 && (v[4] < 0 || v[4] > kTinyMaxN || v[5] < 1 || v[5] > 1024)) continue;
-        if (got == 8 && (v[6] < 0 || v[6] >= kNumSingleVariants || v[7] < 0 || v[7] >= kNumSingleVariants)) continue;
+        if (got >= 8 && (v[6] < 0 || v[6] >= kNumSingleVariants || v[7] < 0 || v[7] >= kNumSingleVariants)) continue;
+        if (got == 9 && (v[8] < 0 || v[8] >= kNumSingleVariants)) continue;
         c->single_variant[0] = v[0];
         c->single_variant[1] = v[1];
         c->tune.variant[0] = v[2];
@@ -130,10 +131,11 @@ void load_tune_cache(DeviceCtx* c)
             c->tune.items_per_warp = v[5];
             c->tune.chunk_log2 = 0;
         }
-        if (got == 8) {
+        if (got >= 8) {
             c->single_variant_short[0] = v[6];
             c->single_variant_short[1] = v[7];
         }
+        if (got == 9) c->single_variant_merged = v[8];
     }
     std::fclose(f);
 }
@@ -156,9 +158,9 @@ static void store_tune_cache(DeviceCtx* c)
     FILE* f = std::fopen(tmp.c_str(), "w");
     if (!f) return;
     for (const auto& l : keep) std::fputs(l.c_str(), f);
-    std::fprintf(f, "%s|%d|%d|%d|%d|%d|%d|%d|%d\n", key.c_str(), c->single_variant[0], c->single_variant[1],
+    std::fprintf(f, "%s|%d|%d|%d|%d|%d|%d|%d|%d|%d\n", key.c_str(), c->single_variant[0], c->single_variant[1],
                  c->tune.variant[0], c->tune.variant[1], c->tune.tiny_cutoff, c->tune.items_per_warp,
-                 c->single_variant_short[0], c->single_variant_short[1]);
+                 c->single_variant_short[0], c->single_variant_short[1], c->single_variant_merged);
     std::fclose(f);
     std::rename(tmp.c_str(), path);
 }
@@ -171,14 +173,14 @@ extern "C" {
 
 int pf3_variant_count(int which)
 {
-    if (which == 0 || which == 2) return kNumSingleVariants;
+    if (which == 0 || which == 2 || which == 3) return kNumSingleVariants;
     if (which == 1) return kNumBatchVariants;
     return PF3_EINVAL;
 }
 
 int pf3_set_variant(int which, int W, int v)
 {
-    if (W < 1 || W > 2 || v < 0 || which < 0 || which > 2) return PF3_EINVAL;
+    if (W < 1 || W > 2 || v < 0 || which < 0 || which > 3 || (which == 3 && W != 1)) return PF3_EINVAL;
     if (v >= (which == 1 ? kNumBatchVariants : kNumSingleVariants)) return PF3_EINVAL;
     int rc;
     DeviceCtx* c = device_ctx(&rc);
@@ -186,6 +188,7 @@ int pf3_set_variant(int which, int W, int v)
     std::lock_guard<std::mutex> g(c->mu);
     if (which == 0) c->single_variant[W - 1] = c->single_variant_short[W - 1] = v;
     else if (which == 2) c->single_variant_short[W - 1] = v;
+    else if (which == 3) c->single_variant_merged = v;
     else c->tune.variant[W - 1] = v;
     return PF3_OK;
 }
@@ -193,7 +196,7 @@ int pf3_set_variant(int which, int W, int v)
 int pf3_variant_info(int which, int v, int* U, int* G, int* min_ctas)
 {
     const KernelVariant* t = nullptr;
-    if ((which == 0 || which == 2) && v >= 0 && v < kNumSingleVariants) t = &kSingleVariants[v];
+    if ((which == 0 || which == 2 || which == 3) && v >= 0 && v < kNumSingleVariants) t = &kSingleVariants[v];
     if (which == 1 && v >= 0 && v < kNumBatchVariants) t = &kBatchVariants[v];
     if (!t) return PF3_EINVAL;
     if (U) *U = t->U;
@@ -211,11 +214,12 @@ int pf3_variant_threads(int which, int v)
 
 int pf3_get_variant(int which, int W)
 {
-    if (W < 1 || W > 2 || which < 0 || which > 2) return PF3_EINVAL;
+    if (W < 1 || W > 2 || which < 0 || which > 3 || (which == 3 && W != 1)) return PF3_EINVAL;
     int rc;
     DeviceCtx* c = device_ctx(&rc);
     if (!c) return rc;
     if (which == 2) return c->single_variant_short[W - 1];
+    if (which == 3) return c->single_variant_merged;
     return which == 0 ? c->single_variant[W - 1] : c->tune.variant[W - 1];
 }
 
@@ -324,6 +328,26 @@ int pf3_autotune_ex(double* single_ms, double* single_short_ms, double* batch_ms
             }
         }
         c->single_variant_short[W - 1] = bestv;
+    }
+    // ---- long launches of a merged matrix (equal columns merged into one
+    // word; its terms are mostly nonzero, so the dense walk runs): J_36 as
+    // the host-pointer calls walk it, 36 rows of two columns of ones, over
+    // 2^33 indices
+    {
+        const int n = 36, m = 2;
+        for (int k = 0; k < n * m; ++k) hA[k] = 1;
+        cudaMemcpy(dA, hA.data(), (size_t)n * m, cudaMemcpyHostToDevice);
+        float best = 1e30f;
+        int bestv = 0;
+        for (int v = 0; v < kNumSingleVariants; ++v) {
+            c->single_variant_merged = v;
+            const float ms = time_ms(s, 2, [&] { enqueue_range(c, dA, n, m, 0, (1ull << 33) - 1, dout, s); });
+            if (v == 0 || ms < kVariantMargin * best) {
+                best = ms;
+                bestv = v;
+            }
+        }
+        c->single_variant_merged = bestv;
     }
     // ---- batch kernel variants, each under the guided split: 8192 matrices
     // of n = 24 (W = 1) and 32 of n = 33 (W = 2), a few grids' worth of work,

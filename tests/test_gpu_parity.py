@@ -511,16 +511,18 @@ def test_autotune_cache_roundtrip(tmp_path):
             "r = b.autotune()\n"
             "t = r['batch_tuning']\n"
             "print(r['single_variant'][1], r['single_variant'][2], r['batch_variant'][1], r['batch_variant'][2],"
-            " t['tiny_cutoff'], t['items_per_warp'], r['single_short_variant'][1], r['single_short_variant'][2])\n"
+            " t['tiny_cutoff'], t['items_per_warp'], r['single_short_variant'][1], r['single_short_variant'][2],"
+            " r['single_merged_variant'])\n"
             ) % root
     first = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
     line = cache.read_text().strip().splitlines()[-1]
-    assert line.split("|")[-8:] == first.stdout.split()
+    assert line.split("|")[-9:] == first.stdout.split()
     code2 = ("import sys; sys.path.insert(0, %r)\n"
              "from paper_2407_20205_gb300 import binding as b\n"
              "t = b.get_batch_tuning()\n"
              "print(b.get_variant(0, 1), b.get_variant(0, 2), b.get_variant(1, 1), b.get_variant(1, 2),"
-             " t['tiny_cutoff'], t['items_per_warp'], b.get_variant(2, 1), b.get_variant(2, 2))\n") % root
+             " t['tiny_cutoff'], t['items_per_warp'], b.get_variant(2, 1), b.get_variant(2, 2), b.get_variant(3, 1))\n"
+             ) % root
     second = subprocess.run([sys.executable, "-c", code2], env=env, capture_output=True, text=True, check=True)
     assert second.stdout.split() == first.stdout.split()
 
