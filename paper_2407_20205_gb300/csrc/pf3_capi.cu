@@ -128,24 +128,32 @@ int check_entries_host(const uint8_t* A, int n)
 bool merge_columns(const uint8_t* A, int n, std::vector<uint8_t>& B, int& m, bool& negate)
 {
     if (n <= 32) return false;
-    std::vector<uint8_t> canon((size_t)n * n);  // class vectors, column by column
-    int mult[PF3_MAX_N] = {};
+    // each class as its canonical vector packed into (nonzero bits, == 2 bits)
+    uint64_t key_m[33], key_s[33];
+    int mult[33] = {};
     int classes = 0;
     bool neg = false;
     for (int j = 0; j < n; ++j) {
-        uint8_t v[PF3_MAX_N];
+        uint64_t km = 0, ks = 0;
         int first = -1;
-        for (int i = 0; i < n; ++i)
-            if (A[(size_t)i * n + j] && first < 0) first = i;
-        const bool flip = first >= 0 && A[(size_t)first * n + j] == 2;
         for (int i = 0; i < n; ++i) {
             const uint8_t e = A[(size_t)i * n + j];
-            v[i] = flip ? (uint8_t)((3 - e) % 3) : e;  // times 2 = times -1 in F3
+            if (!e) continue;
+            if (first < 0) first = i;
+            km |= 1ull << i;
+            if (e == 2) ks |= 1ull << i;
         }
+        const bool flip = first >= 0 && ((ks >> first) & 1ull);
+        if (flip) ks ^= km;  // times 2 = times -1 in F3: 1 <-> 2
         neg ^= flip;
         int k = 0;
-        while (k < classes && std::memcmp(&canon[(size_t)k * n], v, (size_t)n) != 0) ++k;
-        if (k == classes) std::memcpy(&canon[(size_t)classes++ * n], v, (size_t)n);
+        while (k < classes && (key_m[k] != km || key_s[k] != ks)) ++k;
+        if (k == classes) {
+            if (classes == 32) return false;  // m >= classes > 32
+            key_m[k] = km;
+            key_s[k] = ks;
+            ++classes;
+        }
         ++mult[k];
     }
     int cols = 0;
@@ -155,7 +163,8 @@ bool merge_columns(const uint8_t* A, int n, std::vector<uint8_t>& B, int& m, boo
     int col = 0;
     for (int k = 0; k < classes; ++k)
         for (int copy = 0; copy < ((mult[k] & 1) ? 1 : 2); ++copy, ++col)
-            for (int i = 0; i < n; ++i) B[(size_t)i * cols + col] = canon[(size_t)k * n + i];
+            for (int i = 0; i < n; ++i)
+                B[(size_t)i * cols + col] = ((key_m[k] >> i) & 1ull) ? (((key_s[k] >> i) & 1ull) ? 2 : 1) : 0;
     m = cols;
     negate = neg;
     return true;
