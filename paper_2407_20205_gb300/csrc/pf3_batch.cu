@@ -116,10 +116,11 @@ __global__ void __launch_bounds__(kBatchThreads, MINB) batch_kernel(BatchArgs a)
         }
 
         bool bad = false;
+        const int cols = it.cols ? it.cols : n;  // the walk's column count (padding starts there)
         const int rows = n > U ? n : U;
         for (int r = 0; r < rows; ++r) {
             uint32_t mag[2], sgn[2];
-            pack_row_warp(A, n, n, r, lane, mag, sgn, bad);
+            pack_row_warp(A, n, cols, r, lane, mag, sgn, bad);
             if (lane < W) {
                 uint32_t k1, k2p, k2m;
                 row_masks(mag[lane], sgn[lane], k1, k2p, k2m);
@@ -136,15 +137,15 @@ __global__ void __launch_bounds__(kBatchThreads, MINB) batch_kernel(BatchArgs a)
         if (!bad && n > 0) {
             if (it.NB == 0) {
                 // n <= U (serving items): one lane walks all 2^n indices
-                if (lane == 0) walk_generic<W>(tab, n, 0, (n == 64) ? ~0ull : ((1ull << n) - 1), c);
+                if (lane == 0) walk_generic<W>(tab, cols, 0, (n == 64) ? ~0ull : ((1ull << n) - 1), c);
             } else {
                 GroupRows<G, U> R;
                 load_group_rows<W, G, U>(R, tab);
                 uint64_t s, len;
                 split_range(it.NB, 32, (uint64_t)lane, s, len);
                 const uint64_t trip = __shfl_sync(0xFFFFFFFFu, len, 0);
-                const uint64_t done = walk_groups<W, G, U>(tab, R, n, it.B0 + s, len, trip, q, lane, c);
-                if (done < len) walk_dense<W, G, U>(tab, q.dk, n, it.B0 + s + done, len - done, &c);
+                const uint64_t done = walk_groups<W, G, U>(tab, R, cols, it.B0 + s, len, trip, q, lane, c);
+                if (done < len) walk_dense<W, G, U>(tab, q.dk, cols, it.B0 + s + done, len - done, &c);
             }
         }
         const unsigned long long p = warp_sum(c.plus);
@@ -182,7 +183,7 @@ __global__ void slot_init_kernel(const SlotInit* inits, int count, const uint8_t
     const int k = blockIdx.x;
     if (k >= count) return;
     const SlotInit in = inits[k];
-    const int nn = in.n * in.n;
+    const int nn = in.n * (in.cols ? (int)in.cols : in.n);
     uint8_t* dst = mats + (size_t)in.slot * slot_bytes;
     for (int i = threadIdx.x; i < nn; i += blockDim.x) dst[i] = staging[in.src + i];
     if (threadIdx.x == 0) {

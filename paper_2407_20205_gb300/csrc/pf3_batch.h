@@ -22,9 +22,9 @@ struct WorkItem {
     unsigned long long B0;
     unsigned long long NB;
     int mat;                  // matrix index (result slot)
-    int n;
+    int n;                    // rows
     int split;                // -1: the item is the whole matrix; else split slot
-    int pad;
+    int cols;                 // columns walked (0: n, a square matrix; fewer when equal columns were merged)
 };
 
 struct BatchArgs {
@@ -73,9 +73,9 @@ struct BatchPlan {
 struct SlotInit {
     long long src;        // byte offset in the device staging buffer
     int slot;
-    int n;
+    int n;                // rows
     unsigned items;       // work items the job will run in total
-    unsigned pad;
+    unsigned cols;        // columns (0: n)
 };
 
 // warps[cls]: warps of the persistent grid of class cls (W = cls + 1); used

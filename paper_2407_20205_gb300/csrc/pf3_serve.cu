@@ -38,6 +38,10 @@
 
 using namespace pf3;
 
+namespace pf3 {
+bool merge_columns(const uint8_t* A, int n, std::vector<uint8_t>& B, int& m, bool& negate);
+}
+
 namespace {
 
 constexpr int kSlotBytes = kMaxNN;
@@ -54,6 +58,8 @@ enum JobState : int { kQueued = 0, kAdmitted = 1, kDone = 2, kFailed = 3 };
 
 struct Job {
     int n = 0;
+    int m = 0;                // columns walked: n, or fewer when equal columns were merged
+    bool negate = false;      // the merge's sign factor: the result is negated
     int state = kQueued;
     int slot = -1;
     int result = -1;
@@ -158,7 +164,7 @@ bool harvest(pf3_ctx* x, bool block)
         Job& j = x->jobs[tk];
         const unsigned char r = x->h_results[L.buf][j.slot];
         if (r < 3) {
-            j.result = r;
+            j.result = j.negate ? (3 - r) % 3 : r;
             j.state = kDone;
         } else {
             j.state = kFailed;
@@ -274,14 +280,14 @@ bool launch_once(pf3_ctx* x)
         while (!x->pending.empty() && !x->free_slots.empty() && n_inits < x->cfg.max_admit) {
             const int64_t tk = x->pending.front();
             Job& j = x->jobs[tk];
-            const size_t nn = (size_t)j.n * j.n;
+            const size_t nn = (size_t)j.n * j.m;
             if (stage_off + nn > (size_t)x->cfg.max_admit * kSlotBytes) break;
             x->pending.pop_front();
             j.slot = x->free_slots.back();
             x->free_slots.pop_back();
             std::memcpy(x->h_stage[buf] + stage_off, j.A.data(), nn);
             std::vector<uint8_t>().swap(j.A);
-            const int cls = j.n <= 32 ? 0 : 1;
+            const int cls = j.m <= 32 ? 0 : 1;
             const int U = x->U[cls];
             if (j.n <= U) {
                 j.nb = 0;
@@ -298,6 +304,7 @@ bool launch_once(pf3_ctx* x)
             inits[n_inits].src = (long long)stage_off;
             inits[n_inits].slot = j.slot;
             inits[n_inits].n = j.n;
+            inits[n_inits].cols = (unsigned)j.m;
             inits[n_inits].items = (unsigned)j.items_total;
             ++n_inits;
             stage_off += nn;
@@ -314,6 +321,7 @@ bool launch_once(pf3_ctx* x)
                 it.offset = (long long)j.slot * kSlotBytes;
                 it.mat = j.slot;
                 it.n = j.n;
+                it.cols = j.m;
                 it.split = j.slot;
                 uint64_t cost;
                 if (j.nb == 0) {
@@ -323,14 +331,14 @@ bool launch_once(pf3_ctx* x)
                 } else {
                     it.B0 = j.cursor;
                     it.NB = std::min<unsigned long long>(j.per_item, j.nb - j.cursor);
-                    cost = (uint64_t)it.NB << x->U[j.n <= 32 ? 0 : 1];
+                    cost = (uint64_t)it.NB << x->U[j.m <= 32 ? 0 : 1];
                 }
                 if (cost > share && n_items > 0) break;  // the first item always goes
                 share = cost > share ? 0 : share - cost;
                 budget = cost > budget ? 0 : budget - cost;
                 j.cursor += it.NB;
                 ++j.items_issued;
-                cls_items[j.n <= 32 ? 0 : 1].push_back(it);
+                cls_items[j.m <= 32 ? 0 : 1].push_back(it);
                 ++n_items;
                 if (j.items_issued == j.items_total) L.finishing.push_back(tk);
                 if (share == 0) break;
@@ -344,7 +352,7 @@ bool launch_once(pf3_ctx* x)
             auto remaining = [&](int64_t tk) -> uint64_t {
                 const Job& j = x->jobs[tk];
                 if (!j.nb) return 1ull << j.n;
-                const int U = x->U[j.n <= 32 ? 0 : 1];
+                const int U = x->U[j.m <= 32 ? 0 : 1];
                 const uint64_t left = j.nb - j.cursor;
                 return (left >> (64 - U)) ? ~0ull : left << U;  // 2^64 (n = 64) saturates
             };
@@ -632,7 +640,15 @@ int64_t perm_f3_submit(pf3_ctx* x, const uint8_t* A, int n)
         x->cv_done.notify_all();
         return tk;
     }
-    j.A.assign(A, A + (size_t)n * n);
+    // equal columns merged as for perm_f3 (pf3_capi.cu): one plane word
+    // instead of two for requests whose terms are mostly nonzero
+    std::vector<uint8_t> B;
+    if (merge_columns(A, n, B, j.m, j.negate)) {
+        j.A.swap(B);
+    } else {
+        j.m = n;
+        j.A.assign(A, A + (size_t)n * n);
+    }
     x->pending.push_back(tk);
     x->cv_work.notify_one();
     return tk;
