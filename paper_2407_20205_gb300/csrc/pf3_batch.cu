@@ -194,27 +194,6 @@ __global__ void slot_init_kernel(const SlotInit* inits, int count, const uint8_t
     }
 }
 
-// One thread: the counts of a single-matrix range launch (out: plus, minus,
-// result or ~0 on a bad entry) into serving slot `slot`, a range that stood
-// for `items` of the slot's work items; the last finisher of the slot maps
-// its totals to perm mod 3, as the batch kernel's split items do.
-__global__ void fold_range_kernel(const unsigned long long* out, int slot, int n, unsigned items,
-                                  unsigned long long* acc, unsigned* left, uint8_t* results)
-{
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    unsigned long long* a = acc + 2 * slot;
-    atomicAdd(a, out[0]);
-    atomicAdd(a + 1, out[1]);
-    if (out[2] == ~0ull) atomicOr(left + slot, kBadBit);
-    __threadfence();
-    const unsigned before = atomicSub(left + slot, items);
-    if ((before & ~kBadBit) == items) {
-        __threadfence();
-        const unsigned long long P = __ldcg(a), M = __ldcg(a + 1);
-        results[slot] = (before & kBadBit) ? (uint8_t)255 : (uint8_t)perm_from_counts(n, P, M);
-    }
-}
-
 template <int W>
 const void* batch_kernel_ptr(int v)
 {
@@ -248,8 +227,6 @@ cudaError_t launch_batch(int W, int v, const BatchArgs& a, int grid, cudaStream_
 const void* batch_kernel_fn(int W, int v) { return W == 1 ? batch_kernel_ptr<1>(v) : batch_kernel_ptr<2>(v); }
 
 const void* slot_init_fn() { return (const void*)slot_init_kernel; }
-
-const void* fold_range_fn() { return (const void*)fold_range_kernel; }
 
 cudaError_t launch_slot_init(const SlotInit* inits, int count, const uint8_t* staging, uint8_t* mats,
                              int slot_bytes, unsigned long long* acc, unsigned* left, uint8_t* results,

@@ -93,10 +93,6 @@ int batch_max_ctas_per_sm(int W, int v);
 // (args as launch_slot_init's, without the stream; 128 threads per CTA)
 const void* batch_kernel_fn(int W, int v);
 const void* slot_init_fn();
-// one thread folding a single-matrix range launch's counts into a serving
-// slot (args: const unsigned long long* out, int slot, int n, unsigned items,
-// unsigned long long* acc, unsigned* left, uint8_t* results)
-const void* fold_range_fn();
 cudaError_t launch_batch(int W, int v, const BatchArgs& a, int grid, cudaStream_t stream);
 
 }  // namespace pf3

@@ -109,10 +109,6 @@ void plan_chunks(SingleArgs& a, int grid, int threads);
 // plans the chunks for `grid` CTAs
 cudaError_t launch_single(const SingleArgs& a, int v, int grid, cudaStream_t stream);
 
-// variant v of the single-matrix kernel for W plane words (args: one
-// SingleArgs, planned by plan_range and plan_chunks), for graph nodes
-const void* single_kernel_fn(int W, int v);
-
 // CTAs of variant v to launch for this plan given the device (one resident
 // wave at most)
 int single_grid_for(const SingleArgs& a, int v, int sm_count, int max_ctas_per_sm);

@@ -108,16 +108,7 @@ struct pf3_ctx {
     cudaGraph_t graph[2] = {nullptr, nullptr};
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     cudaGraphNode_t g_stage[2] = {}, g_inits[2] = {}, g_items[2] = {}, g_slot[2] = {};
-    cudaGraphNode_t g_batch[2][2] = {};   // [buffer][class]
-    cudaGraphNode_t g_single[2][2] = {};  // [buffer][W - 1]: the oldest large request's range
-    cudaGraphNode_t g_fold[2] = {};
-    // the single-matrix kernel's variants (per W) and per-buffer scratch for
-    // its range launches: 2 partial counts per CTA, ticket / error / cursor
-    // (zero between launches), and its plus, minus, result
-    int svariant[2] = {0, 0};
-    unsigned long long* d_spart[2] = {nullptr, nullptr};
-    unsigned* d_sflags[2] = {nullptr, nullptr};
-    unsigned long long* d_sout[2] = {nullptr, nullptr};
+    cudaGraphNode_t g_batch[2][2] = {};  // [buffer][class]
     // host bookkeeping
     std::mutex mu;
     std::condition_variable cv_done;
@@ -255,42 +246,6 @@ int build_graph(pf3_ctx* x, int b)
         e = cudaGraphAddKernelNode(&x->g_batch[b][cls], g, &prev, 1, &bp);
         if (e == cudaSuccess) dep(x->g_batch[b][cls]);
     }
-    // the oldest large request's range through the single-matrix kernel (one
-    // node per plane width, each with its fixed variant), then the fold of
-    // its counts into the request's slot
-    for (int W = 1; W <= 2 && e == cudaSuccess; ++W) {
-        SingleArgs sa;
-        std::memset(&sa, 0, sizeof(sa));
-        plan_range(1, 0, 1, kSingleVariants[x->svariant[W - 1]].U, sa);
-        sa.A = x->d_mats;
-        sa.partials = x->d_spart[b];
-        sa.ticket = x->d_sflags[b];
-        sa.err = x->d_sflags[b] + 1;
-        sa.cursor = x->d_sflags[b] + 2;
-        sa.out = x->d_sout[b];
-        void* sargs1[] = {(void*)&sa};
-        cudaKernelNodeParams sp = {};
-        sp.func = (void*)single_kernel_fn(W, x->svariant[W - 1]);
-        sp.gridDim = dim3(1);
-        sp.blockDim = dim3(kSingleVariants[x->svariant[W - 1]].threads);
-        sp.kernelParams = sargs1;
-        e = cudaGraphAddKernelNode(&x->g_single[b][W - 1], g, &prev, 1, &sp);
-        if (e == cudaSuccess) dep(x->g_single[b][W - 1]);
-    }
-    {
-        const unsigned long long* out = x->d_sout[b];
-        int slot = 0, n1 = 1;
-        unsigned items1 = 1;
-        void* fargs[] = {(void*)&out, (void*)&slot, (void*)&n1, (void*)&items1, (void*)&x->d_acc, (void*)&x->d_left,
-                         (void*)&x->d_results};
-        cudaKernelNodeParams fp = {};
-        fp.func = (void*)fold_range_fn();
-        fp.gridDim = dim3(1);
-        fp.blockDim = dim3(32);
-        fp.kernelParams = fargs;
-        if (e == cudaSuccess) e = cudaGraphAddKernelNode(&x->g_fold[b], g, &prev, 1, &fp);
-        if (e == cudaSuccess) dep(x->g_fold[b]);
-    }
     // the previous launch (other stream) may still run items of jobs that
     // finish here: results are copied once its kernels are done too
     cudaGraphNode_t n_rec = nullptr, n_wait = nullptr, n_res = nullptr;
@@ -318,13 +273,6 @@ bool launch_once(pf3_ctx* x)
     L.buf = buf;
     int n_inits = 0;
     size_t stage_off = 0;
-    // the oldest large request's range for the single-matrix kernel, if any
-    struct Range {
-        bool on = false;
-        int n = 0, m = 0, slot = 0, U = 0;
-        uint64_t first = 0, blocks = 0;
-        unsigned items = 0;
-    } rng;
     {
         std::lock_guard<std::mutex> g(x->mu);
         if (x->fatal) return false;
@@ -417,34 +365,6 @@ bool launch_once(pf3_ctx* x)
             for (const auto* list : {&small_jobs, &large_jobs})
                 for (int64_t tk : *list) {
                     if (budget == 0 || n_items >= x->cfg.launch_items) break;
-                    Job& j = x->jobs[tk];
-                    if (list == &large_jobs && !rng.on && j.nb) {
-                        // the oldest large request takes what is left of the
-                        // budget as one range (whole work items) through the
-                        // single-matrix kernel, which walks a long range of
-                        // one matrix faster than the batch kernel's items
-                        const int U = x->U[j.m <= 32 ? 0 : 1];
-                        const uint64_t item_cost = j.per_item << U;
-                        uint64_t q = budget / item_cost;
-                        if (q < 1) q = 1;
-                        if (q > j.items_total - j.items_issued) q = j.items_total - j.items_issued;
-                        const uint64_t blocks = std::min<uint64_t>(q * j.per_item, j.nb - j.cursor);
-                        rng.on = true;
-                        rng.n = j.n;
-                        rng.m = j.m;
-                        rng.slot = j.slot;
-                        rng.U = U;
-                        rng.first = j.cursor << U;
-                        rng.blocks = blocks;
-                        rng.items = (unsigned)q;
-                        const uint64_t cost = (blocks >> (64 - U)) ? ~0ull : blocks << U;
-                        budget = cost > budget ? 0 : budget - cost;
-                        j.cursor += blocks;
-                        j.items_issued += q;
-                        x->items += q;
-                        if (j.items_issued == j.items_total) L.finishing.push_back(tk);
-                        continue;
-                    }
                     issue(tk, budget);
                 }
             // drop fully issued jobs from the active list
@@ -456,7 +376,7 @@ bool launch_once(pf3_ctx* x)
         x->items += (uint64_t)(cls_items[0].size() + cls_items[1].size());
     }
     const size_t n1 = cls_items[1].size(), n0 = cls_items[0].size();
-    if (n_inits == 0 && n0 + n1 == 0 && !rng.on) return false;
+    if (n_inits == 0 && n0 + n1 == 0) return false;
     // items: class W = 2 first, then W = 1
     if (n1) std::memcpy(items, cls_items[1].data(), n1 * sizeof(WorkItem));
     if (n0) std::memcpy(items + n1, cls_items[0].data(), n0 * sizeof(WorkItem));
@@ -513,48 +433,6 @@ bool launch_once(pf3_ctx* x)
         }
         if (e == cudaSuccess) e = cudaGraphNodeSetEnabled(ge, x->g_batch[buf][cls], cnt ? 1u : 0u);
     }
-    for (int W = 1; W <= 2 && e == cudaSuccess; ++W) {
-        const bool on = rng.on && (rng.m <= 32 ? 1 : 2) == W;
-        if (on) {
-            const int v = x->svariant[W - 1];
-            SingleArgs sa;
-            std::memset(&sa, 0, sizeof(sa));
-            // inclusive end; the whole 2^64 range of n = 64 wraps to ~0 here
-            const uint64_t last = rng.first + ((rng.blocks << rng.U) - 1);
-            plan_range(rng.n, rng.first, last, kSingleVariants[v].U, sa);
-            sa.m = rng.m;
-            sa.A = x->d_mats + (size_t)rng.slot * kSlotBytes;
-            sa.partials = x->d_spart[buf];
-            sa.ticket = x->d_sflags[buf];
-            sa.err = x->d_sflags[buf] + 1;
-            sa.cursor = x->d_sflags[buf] + 2;
-            sa.out = x->d_sout[buf];
-            const int grid = single_grid_for(sa, v, x->dc->sm_count, single_ctas(x->dc, W, v));
-            plan_chunks(sa, grid, kSingleVariants[v].threads);
-            void* sargs[] = {(void*)&sa};
-            cudaKernelNodeParams sp = {};
-            sp.func = (void*)single_kernel_fn(W, v);
-            sp.gridDim = dim3((unsigned)grid);
-            sp.blockDim = dim3(kSingleVariants[v].threads);
-            sp.kernelParams = sargs;
-            e = cudaGraphExecKernelNodeSetParams(ge, x->g_single[buf][W - 1], &sp);
-        }
-        if (e == cudaSuccess) e = cudaGraphNodeSetEnabled(ge, x->g_single[buf][W - 1], on ? 1u : 0u);
-    }
-    if (e == cudaSuccess && rng.on) {
-        const unsigned long long* out = x->d_sout[buf];
-        int slot = rng.slot, n = rng.n;
-        unsigned items = rng.items;
-        void* fargs[] = {(void*)&out, (void*)&slot, (void*)&n, (void*)&items, (void*)&x->d_acc, (void*)&x->d_left,
-                         (void*)&x->d_results};
-        cudaKernelNodeParams fp = {};
-        fp.func = (void*)fold_range_fn();
-        fp.gridDim = dim3(1);
-        fp.blockDim = dim3(32);
-        fp.kernelParams = fargs;
-        e = cudaGraphExecKernelNodeSetParams(ge, x->g_fold[buf], &fp);
-    }
-    if (e == cudaSuccess) e = cudaGraphNodeSetEnabled(ge, x->g_fold[buf], rng.on ? 1u : 0u);
     if (e == cudaSuccess) e = cudaGraphLaunch(ge, s);
     if (e == cudaSuccess) e = cudaEventRecord(x->ev[buf], s);
     if (e != cudaSuccess) {
@@ -637,7 +515,6 @@ int pf3_create(pf3_ctx** out, const pf3_config* cfg_in)
         x->variant[cls] = dc->tune.variant[cls];
         x->U[cls] = kBatchVariants[x->variant[cls]].U;
         x->grid[cls] = dc->sm_count * batch_ctas(dc, cls + 1, x->variant[cls]);
-        x->svariant[cls] = dc->single_variant[cls];
     }
     bool ok = true;
     for (int b = 0; b < 2 && ok; ++b) {
@@ -656,10 +533,6 @@ int pf3_create(pf3_ctx** out, const pf3_config* cfg_in)
         ok = ok && cudaMallocHost(&x->h_table[b], table_bytes(cfg)) == cudaSuccess;
         ok = ok && cudaMallocHost(&x->h_results[b], (size_t)cfg.max_jobs) == cudaSuccess;
         ok = ok && cudaEventCreateWithFlags(&x->ev[b], cudaEventDisableTiming) == cudaSuccess;
-        ok = ok && cudaMalloc(&x->d_spart[b], sizeof(unsigned long long) * 2 * (size_t)dc->max_grid) == cudaSuccess;
-        ok = ok && cudaMalloc(&x->d_sflags[b], sizeof(unsigned) * 4) == cudaSuccess;
-        ok = ok && cudaMalloc(&x->d_sout[b], sizeof(unsigned long long) * 4) == cudaSuccess;
-        ok = ok && cudaMemset(x->d_sflags[b], 0, sizeof(unsigned) * 4) == cudaSuccess;
     }
     ok = ok && cudaMemset(x->d_results, kPending, (size_t)cfg.max_jobs) == cudaSuccess;
     // both "kernels done" events start recorded (complete), so the first
@@ -716,9 +589,6 @@ void pf3_destroy(pf3_ctx* x)
         cudaFreeHost(x->h_stage[b]);
         cudaFreeHost(x->h_table[b]);
         cudaFreeHost(x->h_results[b]);
-        cudaFree(x->d_spart[b]);
-        cudaFree(x->d_sflags[b]);
-        cudaFree(x->d_sout[b]);
         if (x->ev[b]) cudaEventDestroy(x->ev[b]);
     }
     for (int b = 0; b < 2; ++b) {

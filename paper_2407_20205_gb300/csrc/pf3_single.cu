@@ -283,8 +283,6 @@ void plan_chunks(SingleArgs& a, int grid, int threads)
     a.dynamic = 1;
 }
 
-const void* single_kernel_fn(int W, int v) { return W == 1 ? single_kernel_ptr<1>(v) : single_kernel_ptr<2>(v); }
-
 cudaError_t launch_single(const SingleArgs& args, int v, int grid, cudaStream_t stream)
 {
     SingleArgs a = args;
