@@ -325,6 +325,34 @@ def run_ours(args):
     subsets_step = sum(1 << n for n in SIZES)
     value = subsets_step * args.steps / (total_ms * 1e-3)
 
+    # e2e through the public host-pointer API.  N = 1: perm_f3 per matrix
+    # (input copied in, result out, every call).  N > 1: every rank walks its
+    # Gray range with perm_f3_range_counts (copies in and out every call), the
+    # counts are summed across ranks and the library maps them to the result.
+    e2e_dt = None
+    if world == 1:
+        for n in SIZES:
+            pf3.perm_f3(mats[n])
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            for n in SIZES:
+                r = pf3.perm_f3(mats[n])
+                assert r == results[n]
+        e2e_dt = time.perf_counter() - t0
+    else:
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            for n in SIZES:
+                a, b = ranges[n]
+                p, m = pf3.perm_f3_range_counts(mats[n], a, b) if a <= b else (0, 0)
+                P, M = multirank.allreduce_counts(p, m, device=dev)
+                assert pf3.perm_from_counts(n, P, M) == results[n]
+        barrier()
+        t = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_dt = float(t.item())
+
     line = None
     if rank == 0:
         pk = peaks()
@@ -349,19 +377,11 @@ def run_ours(args):
                         f"{sm_max:.0f} MHz x {lanes:.0f} lanes/clk/SM (ALU pipe issue), of measured clock; "
                         f"executed ALU instructions per subset and ALU pipe busy are ncu figures of this kernel"}
         # e2e through the host-pointer C entry point (copies in and out each call)
-        e2e = None
-        if world == 1:
-            for n in SIZES:
-                pf3.perm_f3(mats[n])
-            t0 = time.perf_counter()
-            for _ in range(args.steps):
-                for n in SIZES:
-                    r = pf3.perm_f3(mats[n])
-                    assert r == results[n]
-            dt = time.perf_counter() - t0
-            e2e = {"value": subsets_step * args.steps / dt, "unit": UNIT,
-                   "h2d_bytes_per_step": int(sum(n * n for n in SIZES)),
-                   "d2h_bytes_per_step": int(24 * len(SIZES))}
+        e2e = {"value": subsets_step * args.steps / e2e_dt, "unit": UNIT,
+               "h2d_bytes_per_step": int(world * sum(n * n for n in SIZES)),
+               "d2h_bytes_per_step": int(world * 24 * len(SIZES)),
+               "path": "perm_f3 per matrix" if world == 1 else
+                       "perm_f3_range_counts per rank, counts summed across ranks, pf3_perm_from_counts"}
         extra = {}
         if not args.no_batch and world == 1:
             extra["batch_n24"] = bench_batch(pf3, torch, dev, stream)
