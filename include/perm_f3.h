@@ -231,6 +231,30 @@ int pf3_job_times(pf3_ctx* ctx, int64_t ticket, uint64_t* submit_ns, uint64_t* d
 /* Launches issued, work items run and requests finished so far. */
 int pf3_serve_stats(pf3_ctx* ctx, uint64_t* launches, uint64_t* items, uint64_t* jobs_done);
 
+/* The serving loop's choice of work items on the host alone (no device is
+ * touched): requests of ns[k] rows and ms[k] columns (ms NULL: ms = ns; fewer
+ * columns stand for a request whose equal columns were merged), all admitted
+ * in index order, planned under cfg (NULL = defaults) with Gray blocks of
+ * 2^U[0] indices for one plane word and 2^U[1] for two, for `launches`
+ * consecutive launches (fewer when every item has been issued).  items (host,
+ * capacity entries; NULL to ask for the count only) receive the items in the
+ * order each launch issues them: request index, launch, class (0 one word, 1
+ * two), first block and number of blocks (0 blocks: the whole request by one
+ * lane), block_log2, and last = 1 on a request's final item.  *num_items
+ * receives their number.  PF3_EINVAL on a bad argument, PF3_ETOOBIG when
+ * capacity is too small. */
+typedef struct {
+    int64_t request;
+    int32_t launch;
+    int32_t cls;
+    uint64_t first_block;
+    uint64_t num_blocks;
+    int32_t block_log2;
+    int32_t last;
+} pf3_serve_item;
+int pf3_serve_plan(const int32_t* ns, const int32_t* ms, int64_t count, const pf3_config* cfg, const int* U,
+                   int launches, pf3_serve_item* items, int64_t capacity, int64_t* num_items);
+
 /* The steady clock the serving times use (ns). */
 uint64_t pf3_now_ns(void);
 

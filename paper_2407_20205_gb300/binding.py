@@ -293,6 +293,38 @@ _lib_now = _sig("pf3_now_ns", ctypes.c_uint64, [])
 _lib_cancel = _sig("pf3_cancel_queued", ctypes.c_int, [ctypes.c_void_p])
 
 
+class ServeItem(ctypes.Structure):
+    _fields_ = [("request", ctypes.c_int64), ("launch", ctypes.c_int32), ("cls", ctypes.c_int32),
+                ("first_block", ctypes.c_uint64), ("num_blocks", ctypes.c_uint64), ("block_log2", ctypes.c_int32),
+                ("last", ctypes.c_int32)]
+
+
+_lib_serve_plan = _sig("pf3_serve_plan", ctypes.c_int,
+                       [ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), ctypes.c_int64,
+                        ctypes.POINTER(PF3Config), _ip, ctypes.c_int, ctypes.POINTER(ServeItem), ctypes.c_int64,
+                        ctypes.POINTER(ctypes.c_int64)])
+
+
+def serve_plan(ns, ms=None, launches: int = 1, U=(9, 9), **cfg_overrides) -> list[dict]:
+    """The serving loop's work items for requests of sizes ns (columns ms),
+    computed on the host (no device needed): one dict per item in issue order."""
+    cfg = config_default()
+    for k, v in cfg_overrides.items():
+        setattr(cfg, k, v)
+    nsa = np.ascontiguousarray(np.asarray(ns, dtype=np.int32))
+    msa = None if ms is None else np.ascontiguousarray(np.asarray(ms, dtype=np.int32))
+    p_ns = nsa.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    p_ms = None if msa is None else msa.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    Ua = (ctypes.c_int * 2)(*U)
+    num = ctypes.c_int64()
+    _check(_lib_serve_plan(p_ns, p_ms, len(nsa), ctypes.byref(cfg), Ua, launches, None, 0, ctypes.byref(num)),
+           "pf3_serve_plan")
+    buf = (ServeItem * max(1, num.value))()
+    _check(_lib_serve_plan(p_ns, p_ms, len(nsa), ctypes.byref(cfg), Ua, launches, buf, num.value, ctypes.byref(num)),
+           "pf3_serve_plan")
+    return [{f: getattr(x, f) for f, _ in ServeItem._fields_} for x in buf[:num.value]]
+
+
 def config_default() -> PF3Config:
     c = PF3Config()
     _lib_cfg_default(ctypes.byref(c))
@@ -613,5 +645,5 @@ def exported_symbols() -> list[str]:
                         "pf3_vec_unpack", "pf3_set_batch_tuning", "pf3_get_batch_tuning",
                         "pf3_autotune_ex", "pf3_batch_plan", "pf3_variant_threads",
                         "pf3_range_plan", "pf3_perm_from_counts", "pf3_vec_pack",
-                        "pf3_column_merge")
+                        "pf3_column_merge", "pf3_serve_plan")
             if hasattr(_lib, n)]

@@ -258,6 +258,101 @@ int build_graph(pf3_ctx* x, int b)
     return cuda_rc(e);
 }
 
+// The work split of an admitted job: Gray blocks of 2^U indices (U of the
+// batch kernel variant of its plane width: one word for at most 32 columns)
+// cut into work items of 2^chunk_log2 indices (Sec. 3.1's blocks of
+// consecutive Gray states); a job of n <= U rows is one item walked by one
+// lane.
+void plan_job_items(Job& j, const pf3_config& cfg, const int U_cls[2])
+{
+    const int U = U_cls[j.m <= 32 ? 0 : 1];
+    if (j.n <= U) {
+        j.nb = 0;
+        j.items_total = 1;
+        return;
+    }
+    j.nb = (j.n == 64) ? (1ull << (64 - U)) : (1ull << (j.n - U));
+    // items per job stay below 2^30 (the device counter's range)
+    const int cl = std::max(std::max(cfg.chunk_log2, U + 5), j.n - 30);
+    j.per_item = (cl - U >= 63) ? j.nb : (1ull << (cl - U));
+    if (j.per_item > j.nb) j.per_item = j.nb;
+    j.items_total = (j.nb + j.per_item - 1) / j.per_item;
+}
+
+// One launch's work items under the serving policy, at most
+// cfg.launch_items and about cfg.launch_budget Gray indices (a job's first
+// item always goes): first every active job whose remaining work is at most
+// 2^small_work_log2 indices, least remaining first, then the others in
+// arrival order (the order of `active`).  Items go to cls_items[0] (one
+// plane word) or [1] (two), and to *issued in issue order when it is given;
+// jobs whose last item was issued are appended to `finishing` and leave
+// `active`.
+void select_items(std::vector<Job>& jobs, std::vector<int64_t>& active, const pf3_config& cfg, const int U_cls[2],
+                  std::vector<WorkItem> (&cls_items)[2], std::vector<int64_t>& finishing,
+                  std::vector<WorkItem>* issued = nullptr)
+{
+    uint64_t budget = cfg.launch_budget;
+    int n_items = 0;
+    auto issue = [&](int64_t tk, uint64_t share) {
+        Job& j = jobs[tk];
+        while (j.items_issued < j.items_total && n_items < cfg.launch_items) {
+            WorkItem it;
+            std::memset(&it, 0, sizeof(it));
+            it.offset = (long long)j.slot * kSlotBytes;
+            it.mat = j.slot;
+            it.n = j.n;
+            it.cols = j.m;
+            it.split = j.slot;
+            uint64_t cost;
+            if (j.nb == 0) {
+                it.B0 = 0;
+                it.NB = 0;
+                cost = 1ull << j.n;
+            } else {
+                it.B0 = j.cursor;
+                it.NB = std::min<unsigned long long>(j.per_item, j.nb - j.cursor);
+                cost = (uint64_t)it.NB << U_cls[j.m <= 32 ? 0 : 1];
+            }
+            if (cost > share && n_items > 0) break;  // the first item always goes
+            share = cost > share ? 0 : share - cost;
+            budget = cost > budget ? 0 : budget - cost;
+            j.cursor += it.NB;
+            ++j.items_issued;
+            cls_items[j.m <= 32 ? 0 : 1].push_back(it);
+            if (issued) issued->push_back(it);
+            ++n_items;
+            if (j.items_issued == j.items_total) finishing.push_back(tk);
+            if (share == 0) break;
+        }
+    };
+    if (active.empty()) return;
+    const int sl = cfg.small_work_log2;
+    const uint64_t small = sl >= 64 ? ~0ull : (1ull << sl);
+    auto remaining = [&](int64_t tk) -> uint64_t {
+        const Job& j = jobs[tk];
+        if (!j.nb) return 1ull << j.n;
+        const int U = U_cls[j.m <= 32 ? 0 : 1];
+        const uint64_t left = j.nb - j.cursor;
+        return (left >> (64 - U)) ? ~0ull : left << U;  // 2^64 (n = 64) saturates
+    };
+    std::vector<int64_t> small_jobs, large_jobs;
+    for (int64_t tk : active)
+        if (jobs[tk].items_issued < jobs[tk].items_total)
+            (remaining(tk) <= small ? small_jobs : large_jobs).push_back(tk);
+    std::stable_sort(small_jobs.begin(), small_jobs.end(),
+                     [&](int64_t a, int64_t b) { return remaining(a) < remaining(b); });
+    for (const auto* list : {&small_jobs, &large_jobs})
+        for (int64_t tk : *list) {
+            if (budget == 0 || n_items >= cfg.launch_items) break;
+            issue(tk, budget);
+        }
+    // drop fully issued jobs from the active list
+    std::vector<int64_t> keep;
+    for (int64_t tk : active)
+        if (jobs[tk].items_issued < jobs[tk].items_total) keep.push_back(tk);
+    active.swap(keep);
+}
+
 // build and enqueue one launch; returns false when there was nothing to do
 bool launch_once(pf3_ctx* x)
 {
@@ -287,19 +382,7 @@ bool launch_once(pf3_ctx* x)
             x->free_slots.pop_back();
             std::memcpy(x->h_stage[buf] + stage_off, j.A.data(), nn);
             std::vector<uint8_t>().swap(j.A);
-            const int cls = j.m <= 32 ? 0 : 1;
-            const int U = x->U[cls];
-            if (j.n <= U) {
-                j.nb = 0;
-                j.items_total = 1;
-            } else {
-                j.nb = (j.n == 64) ? (1ull << (64 - U)) : (1ull << (j.n - U));
-                // items per job stay below 2^30 (the device counter's range)
-                const int cl = std::max(std::max(x->cfg.chunk_log2, U + 5), j.n - 30);
-                j.per_item = (cl - U >= 63) ? j.nb : (1ull << (cl - U));
-                if (j.per_item > j.nb) j.per_item = j.nb;
-                j.items_total = (j.nb + j.per_item - 1) / j.per_item;
-            }
+            plan_job_items(j, x->cfg, x->U);
             j.state = kAdmitted;
             inits[n_inits].src = (long long)stage_off;
             inits[n_inits].slot = j.slot;
@@ -311,68 +394,7 @@ bool launch_once(pf3_ctx* x)
             x->active.push_back(tk);
         }
         // choose items: small jobs first, then the others in arrival order
-        uint64_t budget = x->cfg.launch_budget;
-        int n_items = 0;
-        auto issue = [&](int64_t tk, uint64_t share) {
-            Job& j = x->jobs[tk];
-            while (j.items_issued < j.items_total && n_items < x->cfg.launch_items) {
-                WorkItem it;
-                std::memset(&it, 0, sizeof(it));
-                it.offset = (long long)j.slot * kSlotBytes;
-                it.mat = j.slot;
-                it.n = j.n;
-                it.cols = j.m;
-                it.split = j.slot;
-                uint64_t cost;
-                if (j.nb == 0) {
-                    it.B0 = 0;
-                    it.NB = 0;
-                    cost = 1ull << j.n;
-                } else {
-                    it.B0 = j.cursor;
-                    it.NB = std::min<unsigned long long>(j.per_item, j.nb - j.cursor);
-                    cost = (uint64_t)it.NB << x->U[j.m <= 32 ? 0 : 1];
-                }
-                if (cost > share && n_items > 0) break;  // the first item always goes
-                share = cost > share ? 0 : share - cost;
-                budget = cost > budget ? 0 : budget - cost;
-                j.cursor += it.NB;
-                ++j.items_issued;
-                cls_items[j.m <= 32 ? 0 : 1].push_back(it);
-                ++n_items;
-                if (j.items_issued == j.items_total) L.finishing.push_back(tk);
-                if (share == 0) break;
-            }
-        };
-        if (!x->active.empty()) {
-            // small jobs (remaining work at most 2^small_work_log2), least
-            // remaining first; then the rest in arrival order
-            const int sl = x->cfg.small_work_log2;
-            const uint64_t small = sl >= 64 ? ~0ull : (1ull << sl);
-            auto remaining = [&](int64_t tk) -> uint64_t {
-                const Job& j = x->jobs[tk];
-                if (!j.nb) return 1ull << j.n;
-                const int U = x->U[j.m <= 32 ? 0 : 1];
-                const uint64_t left = j.nb - j.cursor;
-                return (left >> (64 - U)) ? ~0ull : left << U;  // 2^64 (n = 64) saturates
-            };
-            std::vector<int64_t> small_jobs, large_jobs;
-            for (int64_t tk : x->active)
-                if (x->jobs[tk].items_issued < x->jobs[tk].items_total)
-                    (remaining(tk) <= small ? small_jobs : large_jobs).push_back(tk);
-            std::stable_sort(small_jobs.begin(), small_jobs.end(),
-                             [&](int64_t a, int64_t b) { return remaining(a) < remaining(b); });
-            for (const auto* list : {&small_jobs, &large_jobs})
-                for (int64_t tk : *list) {
-                    if (budget == 0 || n_items >= x->cfg.launch_items) break;
-                    issue(tk, budget);
-                }
-            // drop fully issued jobs from the active list
-            std::vector<int64_t> keep;
-            for (int64_t tk : x->active)
-                if (x->jobs[tk].items_issued < x->jobs[tk].items_total) keep.push_back(tk);
-            x->active.swap(keep);
-        }
+        select_items(x->jobs, x->active, x->cfg, x->U, cls_items, L.finishing);
         x->items += (uint64_t)(cls_items[0].size() + cls_items[1].size());
     }
     const size_t n1 = cls_items[1].size(), n0 = cls_items[0].size();
@@ -494,16 +516,66 @@ void pf3_config_default(pf3_config* cfg)
     cfg->launch_budget = 1ull << 33;
 }
 
+static bool valid_config(const pf3_config& cfg)
+{
+    return !(cfg.max_jobs < 1 || cfg.max_jobs > (1 << 20) || cfg.queue_depth < 1 || cfg.chunk_log2 < 13 ||
+             cfg.chunk_log2 > 62 || cfg.launch_items < 1 || cfg.max_admit < 1 || cfg.launch_budget < 1 ||
+             cfg.small_work_log2 < 0 || cfg.small_work_log2 > 64);
+}
+
+int pf3_serve_plan(const int32_t* ns, const int32_t* ms, int64_t count, const pf3_config* cfg_in, const int* U,
+                   int launches, pf3_serve_item* items, int64_t capacity, int64_t* num_items)
+{
+    if (count < 0 || (count > 0 && !ns) || !U || launches < 1 || !num_items || capacity < 0) return PF3_EINVAL;
+    pf3_config cfg;
+    pf3_config_default(&cfg);
+    if (cfg_in) cfg = *cfg_in;
+    if (!valid_config(cfg)) return PF3_EINVAL;
+    if (U[0] < 1 || U[0] > 20 || U[1] < 1 || U[1] > 20) return PF3_EINVAL;
+    std::vector<Job> jobs((size_t)count);
+    std::vector<int64_t> active;
+    for (int64_t k = 0; k < count; ++k) {
+        const int n = ns[k], m = ms ? ms[k] : n;
+        if (n < 1 || n > PF3_MAX_N || m < 1 || m > n) return PF3_EINVAL;
+        Job& j = jobs[(size_t)k];
+        j.n = n;
+        j.m = m;
+        j.slot = (int)k;
+        plan_job_items(j, cfg, U);
+        active.push_back(k);
+    }
+    int64_t total = 0;
+    for (int l = 0; l < launches && !active.empty(); ++l) {
+        std::vector<WorkItem> cls_items[2], all;
+        std::vector<int64_t> finishing;
+        select_items(jobs, active, cfg, U, cls_items, finishing, &all);
+        for (const WorkItem& it : all) {
+            if (items && total < capacity) {
+                pf3_serve_item& o = items[total];
+                const Job& j = jobs[(size_t)it.mat];
+                o.request = it.mat;
+                o.launch = l;
+                o.cls = j.m <= 32 ? 0 : 1;
+                o.first_block = it.B0;
+                o.num_blocks = it.NB;
+                o.block_log2 = U[o.cls];
+                o.last = (j.nb == 0 || it.B0 + it.NB == j.nb) ? 1 : 0;
+            }
+            ++total;
+        }
+    }
+    *num_items = total;
+    if (items && capacity < total) return PF3_ETOOBIG;
+    return PF3_OK;
+}
+
 int pf3_create(pf3_ctx** out, const pf3_config* cfg_in)
 {
     if (!out) return PF3_EINVAL;
     pf3_config cfg;
     pf3_config_default(&cfg);
     if (cfg_in) cfg = *cfg_in;
-    if (cfg.max_jobs < 1 || cfg.max_jobs > (1 << 20) || cfg.queue_depth < 1 || cfg.chunk_log2 < 13 ||
-        cfg.chunk_log2 > 62 || cfg.launch_items < 1 || cfg.max_admit < 1 || cfg.launch_budget < 1 ||
-        cfg.small_work_log2 < 0 || cfg.small_work_log2 > 64)
-        return PF3_EINVAL;
+    if (!valid_config(cfg)) return PF3_EINVAL;
     int rc;
     DeviceCtx* dc = device_ctx(&rc);
     if (!dc) return rc;

@@ -161,7 +161,8 @@ def test_struct_layouts_match_the_binding(tmp_path):
     compiler lays them out, equal the ctypes Structures the binding passes."""
     import ctypes
     from paper_2407_20205_gb300 import binding
-    structs = {"pf3_config": binding.PF3Config, "pf3_plan_item": binding.PlanItem}
+    structs = {"pf3_config": binding.PF3Config, "pf3_plan_item": binding.PlanItem,
+               "pf3_serve_item": binding.ServeItem}
     lines = []
     for cname, cls in structs.items():
         lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
