@@ -170,8 +170,6 @@ bool merge_columns(const uint8_t* A, int n, std::vector<uint8_t>& B, int& m, boo
     return true;
 }
 
-// enqueue the single-matrix range walk on `stream` (dA on device: n rows of
-// m columns, m = n unless the columns were merged)
 int enqueue_range(DeviceCtx* c, const uint8_t* dA, int n, int m, uint64_t first, uint64_t last,
                   unsigned long long* d_out, cudaStream_t stream)
 {

@@ -83,6 +83,14 @@ struct DeviceCtx {
 
 int cuda_rc(cudaError_t e);
 DeviceCtx* device_ctx(int* rc);
+// enqueue the single-matrix walk of Gray indices [first, last] of the device
+// matrix dA (n rows of m columns; m = n unless equal columns were merged) on
+// `stream`, results to d_out (plus, minus, perm mod 3)
+int enqueue_range(DeviceCtx* c, const uint8_t* dA, int n, int m, uint64_t first, uint64_t last,
+                  unsigned long long* d_out, cudaStream_t stream);
+// the equal-column merge of the host-pointer calls (pf3_capi.cu): on true, B
+// (n x m, row-major), m and negate describe the matrix to walk instead of A
+bool merge_columns(const uint8_t* A, int n, std::vector<uint8_t>& B, int& m, bool& negate);
 // Order work on `stream` that uses the buffers guarded by `ev` after the
 // previous user of those buffers (cudaStreamWaitEvent), and mark its end
 // (cudaEventRecord).  Inside a stream capture both do nothing: ordering the

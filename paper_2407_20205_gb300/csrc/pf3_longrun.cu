@@ -24,12 +24,6 @@
 #include "pf3_context.h"
 #include "pf3_internal.h"
 
-namespace pf3 {
-int enqueue_range(DeviceCtx* c, const uint8_t* dA, int n, int m, uint64_t first, uint64_t last,
-                  unsigned long long* d_out, cudaStream_t stream);
-bool merge_columns(const uint8_t* A, int n, std::vector<uint8_t>& B, int& m, bool& negate);
-}
-
 using namespace pf3;
 
 namespace {

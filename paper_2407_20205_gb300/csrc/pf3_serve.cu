@@ -38,10 +38,6 @@
 
 using namespace pf3;
 
-namespace pf3 {
-bool merge_columns(const uint8_t* A, int n, std::vector<uint8_t>& B, int& m, bool& negate);
-}
-
 namespace {
 
 constexpr int kSlotBytes = kMaxNN;

@@ -25,9 +25,6 @@
 
 namespace pf3 {
 
-int enqueue_range(DeviceCtx* c, const uint8_t* dA, int n, int m, uint64_t first, uint64_t last,
-                  unsigned long long* d_out, cudaStream_t stream);
-
 namespace {
 
 void sample_matrix(uint8_t* A, int n, uint64_t seed)
