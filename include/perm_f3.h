@@ -242,7 +242,7 @@ int pf3_serve_stats(pf3_ctx* ctx, uint64_t* launches, uint64_t* items, uint64_t*
  * two), first block and number of blocks (0 blocks: the whole request by one
  * lane), block_log2, and last = 1 on a request's final item.  *num_items
  * receives their number.  PF3_EINVAL on a bad argument, PF3_ETOOBIG when
- * capacity is too small. */
+ * capacity is too small (nothing written to items). */
 typedef struct {
     int64_t request;
     int32_t launch;

@@ -540,28 +540,28 @@ int pf3_serve_plan(const int32_t* ns, const int32_t* ms, int64_t count, const pf
         plan_job_items(j, cfg, U);
         active.push_back(k);
     }
-    int64_t total = 0;
+    std::vector<pf3_serve_item> out;
     for (int l = 0; l < launches && !active.empty(); ++l) {
         std::vector<WorkItem> cls_items[2], all;
         std::vector<int64_t> finishing;
         select_items(jobs, active, cfg, U, cls_items, finishing, &all);
         for (const WorkItem& it : all) {
-            if (items && total < capacity) {
-                pf3_serve_item& o = items[total];
-                const Job& j = jobs[(size_t)it.mat];
-                o.request = it.mat;
-                o.launch = l;
-                o.cls = j.m <= 32 ? 0 : 1;
-                o.first_block = it.B0;
-                o.num_blocks = it.NB;
-                o.block_log2 = U[o.cls];
-                o.last = (j.nb == 0 || it.B0 + it.NB == j.nb) ? 1 : 0;
-            }
-            ++total;
+            const Job& j = jobs[(size_t)it.mat];
+            pf3_serve_item o;
+            o.request = it.mat;
+            o.launch = l;
+            o.cls = j.m <= 32 ? 0 : 1;
+            o.first_block = it.B0;
+            o.num_blocks = it.NB;
+            o.block_log2 = U[o.cls];
+            o.last = (j.nb == 0 || it.B0 + it.NB == j.nb) ? 1 : 0;
+            out.push_back(o);
         }
     }
-    *num_items = total;
-    if (items && capacity < total) return PF3_ETOOBIG;
+    *num_items = (int64_t)out.size();
+    if (!items) return PF3_OK;
+    if (capacity < (int64_t)out.size()) return PF3_ETOOBIG;  // nothing written
+    std::copy(out.begin(), out.end(), items);
     return PF3_OK;
 }
 

@@ -106,3 +106,20 @@ def test_bad_arguments(pf3):
             pf3.serve_plan(ns, ms, launches=1, U=u)
     with pytest.raises(pf3.PF3Error):
         pf3.serve_plan([20], launches=1, U=U, chunk_log2=5)
+
+
+def test_too_small_a_buffer_writes_nothing(pf3):
+    import ctypes
+    import numpy as np
+    b = pf3
+    ns = np.array([30, 35], np.int32)
+    cfg = b.config_default()
+    Ua = (ctypes.c_int * 2)(*U)
+    num = ctypes.c_int64()
+    buf = (b.ServeItem * 2)()
+    for x in buf:
+        x.request = -7
+    rc = b._lib_serve_plan(ns.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), None, 2, ctypes.byref(cfg), Ua, 50,
+                           buf, 2, ctypes.byref(num))
+    assert rc == b.PF3_ETOOBIG and num.value > 2
+    assert all(x.request == -7 for x in buf)
