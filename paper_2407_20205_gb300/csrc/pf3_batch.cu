@@ -76,7 +76,10 @@ __device__ __forceinline__ int tiny_perm(TinyTable& T, const uint8_t* A, int n, 
     return (int)perm_from_counts(n, p, q);
 }
 
-template <int W, int U, int G, int MINB>
+// COLS: the work items may carry a column count below n (serving merges equal
+// columns at submit); the batch API's items are square and use the instance
+// without it
+template <int W, int U, int G, int MINB, bool COLS>
 __global__ void __launch_bounds__(kBatchThreads, MINB) batch_kernel(BatchArgs a)
 {
     __shared__ RowTable<W> tabs[kBatchThreads / 32];
@@ -116,7 +119,7 @@ __global__ void __launch_bounds__(kBatchThreads, MINB) batch_kernel(BatchArgs a)
         }
 
         bool bad = false;
-        const int cols = it.cols ? it.cols : n;  // the walk's column count (padding starts there)
+        const int cols = (COLS && it.cols) ? it.cols : n;  // the walk's column count (padding starts there)
         const int rows = n > U ? n : U;
         for (int r = 0; r < rows; ++r) {
             uint32_t mag[2], sgn[2];
@@ -194,16 +197,16 @@ __global__ void slot_init_kernel(const SlotInit* inits, int count, const uint8_t
     }
 }
 
-template <int W>
+template <int W, bool COLS>
 const void* batch_kernel_ptr(int v)
 {
     switch (v) {
-    case 0: return (const void*)batch_kernel<W, kBatchVariants[0].U, kBatchVariants[0].G, kBatchVariants[0].min_ctas>;
-    case 1: return (const void*)batch_kernel<W, kBatchVariants[1].U, kBatchVariants[1].G, kBatchVariants[1].min_ctas>;
-    case 2: return (const void*)batch_kernel<W, kBatchVariants[2].U, kBatchVariants[2].G, kBatchVariants[2].min_ctas>;
-    case 3: return (const void*)batch_kernel<W, kBatchVariants[3].U, kBatchVariants[3].G, kBatchVariants[3].min_ctas>;
-    case 4: return (const void*)batch_kernel<W, kBatchVariants[4].U, kBatchVariants[4].G, kBatchVariants[4].min_ctas>;
-    default: return (const void*)batch_kernel<W, kBatchVariants[5].U, kBatchVariants[5].G, kBatchVariants[5].min_ctas>;
+    case 0: return (const void*)batch_kernel<W, kBatchVariants[0].U, kBatchVariants[0].G, kBatchVariants[0].min_ctas, COLS>;
+    case 1: return (const void*)batch_kernel<W, kBatchVariants[1].U, kBatchVariants[1].G, kBatchVariants[1].min_ctas, COLS>;
+    case 2: return (const void*)batch_kernel<W, kBatchVariants[2].U, kBatchVariants[2].G, kBatchVariants[2].min_ctas, COLS>;
+    case 3: return (const void*)batch_kernel<W, kBatchVariants[3].U, kBatchVariants[3].G, kBatchVariants[3].min_ctas, COLS>;
+    case 4: return (const void*)batch_kernel<W, kBatchVariants[4].U, kBatchVariants[4].G, kBatchVariants[4].min_ctas, COLS>;
+    default: return (const void*)batch_kernel<W, kBatchVariants[5].U, kBatchVariants[5].G, kBatchVariants[5].min_ctas, COLS>;
     }
 }
 
@@ -212,19 +215,19 @@ const void* batch_kernel_ptr(int v)
 int batch_max_ctas_per_sm(int W, int v)
 {
     int ctas = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, W == 1 ? batch_kernel_ptr<1>(v) : batch_kernel_ptr<2>(v),
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, W == 1 ? batch_kernel_ptr<1, false>(v) : batch_kernel_ptr<2, false>(v),
                                                   kBatchThreads, 0);
     return ctas > 0 ? ctas : 1;
 }
 
 cudaError_t launch_batch(int W, int v, const BatchArgs& a, int grid, cudaStream_t stream)
 {
-    const void* fn = W == 1 ? batch_kernel_ptr<1>(v) : batch_kernel_ptr<2>(v);
+    const void* fn = W == 1 ? batch_kernel_ptr<1, false>(v) : batch_kernel_ptr<2, false>(v);
     void* args[] = {(void*)&a};
     return cudaLaunchKernel(fn, dim3(grid), dim3(kBatchThreads), args, 0, stream);
 }
 
-const void* batch_kernel_fn(int W, int v) { return W == 1 ? batch_kernel_ptr<1>(v) : batch_kernel_ptr<2>(v); }
+const void* batch_kernel_fn(int W, int v) { return W == 1 ? batch_kernel_ptr<1, true>(v) : batch_kernel_ptr<2, true>(v); }
 
 const void* slot_init_fn() { return (const void*)slot_init_kernel; }
 

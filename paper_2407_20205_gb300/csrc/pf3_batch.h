@@ -89,7 +89,9 @@ cudaError_t launch_slot_init(const SlotInit* inits, int count, const uint8_t* st
                              cudaStream_t stream);
 int batch_max_ctas_per_sm(int W, int v);
 // the kernels themselves, for graph nodes: variant v of the batch kernel for
-// plane width W (args: one BatchArgs), and the serving slot set-up kernel
+// plane width W that reads each work item's column count (args: one
+// BatchArgs; launch_batch runs the instance for square items), and the
+// serving slot set-up kernel
 // (args as launch_slot_init's, without the stream; 128 threads per CTA)
 const void* batch_kernel_fn(int W, int v);
 const void* slot_init_fn();
