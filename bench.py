@@ -509,7 +509,8 @@ def bench_dense(pf3, torch, dev, stream, n=39, reps=3):
     thirds of its terms nonzero, every warp in the dense walk) and the seeded
     uniform n x n matrix, each a full 2^n walk in one launch through the
     device-pointer call (A as it is), and J_n through the host-pointer call,
-    which merges its equal columns first."""
+    which merges its equal columns first and then either walks the merged
+    matrix (class limit 0) or counts it by column-sum vector (the default)."""
     from paper_2407_20205_gb300 import inputs
     out = torch.zeros(3, dtype=torch.int64, device=dev)
     res = {}
@@ -525,19 +526,28 @@ def bench_dense(pf3, torch, dev, stream, n=39, reps=3):
             e1.record(stream)
         stream.synchronize()
         res[name] = {"ms": e0.elapsed_time(e1) / reps, "perm": int(out[2].cpu())}
-    # the host-pointer call on J_n: its equal columns are merged first (one
-    # plane word instead of two); wall clock around perm_f3, copies included
+    # the host-pointer call on J_n: its equal columns merge into one or two,
+    # which are counted by column-sum vector; with the class limit at 0 the
+    # merged matrix (one plane word) is walked.  Wall clock around perm_f3,
+    # copies included.
     J = np.ones((n, n), np.uint8)
-    pf3.perm_f3(J)
-    t = []
-    for _ in range(reps):
-        t0 = time.perf_counter()
-        r = pf3.perm_f3(J)
-        t.append((time.perf_counter() - t0) * 1e3)
-    res["ones_merged_host_call"] = {"ms": float(min(t)), "perm": r}
+    keep = pf3.get_class_limit()
+    for key, limit in (("ones_merged_host_call", 0), ("ones_by_class_host_call", keep)):
+        pf3.set_class_limit(limit)
+        try:
+            pf3.perm_f3(J)
+            t = []
+            for _ in range(reps):
+                t0 = time.perf_counter()
+                r = pf3.perm_f3(J)
+                t.append((time.perf_counter() - t0) * 1e3)
+        finally:
+            pf3.set_class_limit(keep)
+        res[key] = {"ms": float(min(t)), "perm": r}
     res["n"] = n
     res["ratio"] = res["ones"]["ms"] / res["uniform"]["ms"]
     res["ratio_merged"] = res["ones_merged_host_call"]["ms"] / res["uniform"]["ms"]
+    res["ratio_by_class"] = res["ones_by_class_host_call"]["ms"] / res["uniform"]["ms"]
     return res
 
 

@@ -59,6 +59,9 @@ extern "C" {
 #define PF3_ETOOBIG (-8)     /* request larger than a fixed buffer: no-allocation scratch, output array */
 
 #define PF3_MAX_N 64
+/* Widest merged matrix counted by column-sum vector (pf3_class_counts): its
+ * table holds 2 * 3^8 counters. */
+#define PF3_CLASS_MAX_COLS 8
 /* Most matrices in one batch call (work items index matrices with 32-bit
  * integers); larger counts are rejected with PF3_EINVAL. */
 #define PF3_MAX_BATCH 2147483583LL
@@ -138,7 +141,10 @@ int perm_f3_range_counts_noalloc(const uint8_t* dA, int n, uint64_t first, uint6
  * when pf3_longrun_cancel(1) was called (PF3_ECANCELED; checked before each
  * launch); the counts so far are returned and saved either way.  *finished = 1 once the whole range is done;
  * *next_index is the first index not yet walked (0 when finished).  result
- * (may be NULL): perm(A) mod 3 in {0,1,2} once finished, untouched before. */
+ * (may be NULL): perm(A) mod 3 in {0,1,2} once finished, untouched before.
+ * A fresh run (no checkpoint to resume) of a matrix whose equal columns merge
+ * into at most pf3_get_class_limit() columns (n > 32) is counted by column-sum
+ * vector (pf3_class_counts) in one launch instead. */
 #define PF3_LONGRUN_MAX_CHUNK_LOG2 44
 int pf3_longrun(const uint8_t* A, int n, int chunk_log2, const char* checkpoint_path, double max_seconds,
                 uint64_t* plus, uint64_t* minus, uint64_t* next_index, int* finished, int* result);
@@ -194,6 +200,10 @@ typedef struct pf3_config {
                                 are served first, least remaining first; the others
                                 in arrival order (0..64); default 33 */
     uint64_t launch_budget;  /* Gray indices per launch (soft cap); default 2^33 */
+    int32_t class_max_cols;  /* a request whose merged matrix (n > 32) has at most this
+                                many columns is counted by column-sum vector
+                                (pf3_class_counts) in the launch that admits it, not
+                                walked; 0..PF3_CLASS_MAX_COLS, default PF3_CLASS_MAX_COLS */
 } pf3_config;
 
 typedef struct pf3_ctx pf3_ctx;
@@ -316,6 +326,28 @@ int pf3_pack(const uint8_t* A, int n, uint64_t* mag, uint64_t* sgn);
  * 0 when it does not (nothing written), or a negative code.  Host only; no
  * device is touched.  (Not in the paper: an exact rewriting of Eq. (2).) */
 int pf3_column_merge(const uint8_t* A, int n, uint8_t* B, int* m, int* negate);
+
+/* Ryser counts (plus, minus as above) of A by column-sum vector.  A term
+ * depends on its row subset S only through the column sums over S (a point
+ * of F3^m) and the parity of |S|; the number of subsets on each of those
+ * 2 * 3^m pairs follows row by row, and the counts are read off the pairs
+ * whose sums are all nonzero.  Exactly the walk's counts, in n * 3^m steps
+ * instead of 2^n.  A's columns are first merged as by pf3_column_merge (here
+ * for any n); when the merged matrix has at most PF3_CLASS_MAX_COLS columns
+ * the counts are computed on the device (one CTA) and 1 is returned, else 0
+ * and nothing is written.  A: host, n*n bytes, 1 <= n <= 64.  perm_f3,
+ * perm_f3_counts, pf3_longrun (a fresh run) and the serving contexts take
+ * this route for n > 32 when the merged width is at most the limit set by
+ * pf3_set_class_limit (perm_f3 and the long run) or pf3_config.class_max_cols
+ * (serving).  (Not in the paper: an exact regrouping of Eq. (2)'s sum.) */
+int pf3_class_counts(const uint8_t* A, int n, uint64_t* plus, uint64_t* minus);
+
+/* Widest merged matrix (0..PF3_CLASS_MAX_COLS) that perm_f3, perm_f3_counts
+ * and a fresh pf3_longrun count by column-sum vector instead of walking, on
+ * the current device; 0 walks every matrix.  Default PF3_CLASS_MAX_COLS.
+ * pf3_get_class_limit returns the current value or a negative code. */
+int pf3_set_class_limit(int max_cols);
+int pf3_get_class_limit(void);
 
 /* Integer-pipe microbenchmark (the roofline denominator of the walk).  kind:
  * 0 LOP3, 1 IMAD, 2 IADD, 3 LOP3+IMAD, 4 full row step (3 LOP3 + compare),

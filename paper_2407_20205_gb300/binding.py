@@ -278,7 +278,7 @@ def longrun_cancel(on: bool = True) -> None:
 class PF3Config(ctypes.Structure):
     _fields_ = [("max_jobs", ctypes.c_int32), ("queue_depth", ctypes.c_int32), ("chunk_log2", ctypes.c_int32),
                 ("launch_items", ctypes.c_int32), ("max_admit", ctypes.c_int32), ("small_work_log2", ctypes.c_int32),
-                ("launch_budget", ctypes.c_uint64)]
+                ("launch_budget", ctypes.c_uint64), ("class_max_cols", ctypes.c_int32)]
 
 
 _lib_cfg_default = _sig("pf3_config_default", None, [ctypes.POINTER(PF3Config)])
@@ -472,6 +472,31 @@ def vec_pack(X) -> tuple[np.ndarray, np.ndarray]:
 _lib_colmerge = _sig("pf3_column_merge", ctypes.c_int, [_u8p, ctypes.c_int, _u8p, _ip, _ip])
 
 
+_lib_class_counts = _sig("pf3_class_counts", ctypes.c_int, [_u8p, ctypes.c_int, _u64p, _u64p])
+_lib_set_class_limit = _sig("pf3_set_class_limit", ctypes.c_int, [ctypes.c_int])
+_lib_get_class_limit = _sig("pf3_get_class_limit", ctypes.c_int, [])
+CLASS_MAX_COLS = 8
+
+
+def class_counts(A):
+    """(plus, minus) of A counted by column-sum vector on the device, or None
+    when A's columns merge into more than CLASS_MAX_COLS columns."""
+    a, p, n = _square(A)
+    P, M = ctypes.c_uint64(), ctypes.c_uint64()
+    rc = _check(_lib_class_counts(p, n, ctypes.byref(P), ctypes.byref(M)), "pf3_class_counts")
+    return (P.value, M.value) if rc == 1 else None
+
+
+def set_class_limit(max_cols: int) -> None:
+    """Widest merged matrix perm_f3, perm_f3_counts and a fresh long run count
+    by column-sum vector (0: walk every matrix)."""
+    _check(_lib_set_class_limit(max_cols), "pf3_set_class_limit")
+
+
+def get_class_limit() -> int:
+    return _check(_lib_get_class_limit(), "pf3_get_class_limit")
+
+
 def column_merge(A):
     """The column merge the host-pointer single-matrix calls apply: (B, negate)
     with B the n x m matrix walked instead of A, or None when A is walked as
@@ -645,5 +670,6 @@ def exported_symbols() -> list[str]:
                         "pf3_vec_unpack", "pf3_set_batch_tuning", "pf3_get_batch_tuning",
                         "pf3_autotune_ex", "pf3_batch_plan", "pf3_variant_threads",
                         "pf3_range_plan", "pf3_perm_from_counts", "pf3_vec_pack",
-                        "pf3_column_merge", "pf3_serve_plan")
+                        "pf3_column_merge", "pf3_serve_plan", "pf3_class_counts", "pf3_set_class_limit",
+                        "pf3_get_class_limit")
             if hasattr(_lib, n)]

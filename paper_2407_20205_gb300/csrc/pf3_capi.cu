@@ -119,18 +119,14 @@ int check_entries_host(const uint8_t* A, int n)
 // as one copy of v_c for odd and two copies for even multiplicity.  Walking
 // the n-row matrix of those columns instead of A changes every term by the
 // one factor prod_j l_j, so the +1/-1 counts are A's, swapped when that
-// factor is -1.  Worth it when the merged matrix fits one plane word and A
-// does not (n > 32, m <= 32): matrices with many equal columns are the ones
-// whose terms are mostly nonzero (the dense walk), where the second word
-// doubles the work per state.
-// On true, B (n rows x m columns, row-major), m and negate describe the merged
-// matrix; on false nothing is written and A is walked as it is.
-bool merge_columns(const uint8_t* A, int n, std::vector<uint8_t>& B, int& m, bool& negate)
+// factor is -1.
+// On true (the merged matrix has at most max_cols columns), B (n rows x m
+// columns, row-major), m and negate describe it; on false nothing is written.
+bool column_classes(const uint8_t* A, int n, int max_cols, std::vector<uint8_t>& B, int& m, bool& negate)
 {
-    if (n <= 32) return false;
     // each class as its canonical vector packed into (nonzero bits, == 2 bits)
-    uint64_t key_m[33], key_s[33];
-    int mult[33] = {};
+    uint64_t key_m[64], key_s[64];
+    int mult[64] = {};
     int classes = 0;
     bool neg = false;
     for (int j = 0; j < n; ++j) {
@@ -149,7 +145,7 @@ bool merge_columns(const uint8_t* A, int n, std::vector<uint8_t>& B, int& m, boo
         int k = 0;
         while (k < classes && (key_m[k] != km || key_s[k] != ks)) ++k;
         if (k == classes) {
-            if (classes == 32) return false;  // m >= classes > 32
+            if (classes == max_cols) return false;  // m >= classes > max_cols
             key_m[k] = km;
             key_s[k] = ks;
             ++classes;
@@ -158,7 +154,7 @@ bool merge_columns(const uint8_t* A, int n, std::vector<uint8_t>& B, int& m, boo
     }
     int cols = 0;
     for (int k = 0; k < classes; ++k) cols += (mult[k] & 1) ? 1 : 2;
-    if (cols > 32) return false;
+    if (cols > max_cols) return false;
     B.assign((size_t)n * cols, 0);
     int col = 0;
     for (int k = 0; k < classes; ++k)
@@ -168,6 +164,15 @@ bool merge_columns(const uint8_t* A, int n, std::vector<uint8_t>& B, int& m, boo
     m = cols;
     negate = neg;
     return true;
+}
+
+// The merge the host-pointer calls apply before walking: worth it when the
+// merged matrix fits one plane word and A does not (n > 32, m <= 32).
+// Matrices with many equal columns are the ones whose terms are mostly nonzero
+// (the dense walk), where the second word doubles the work per state.
+bool merge_columns(const uint8_t* A, int n, std::vector<uint8_t>& B, int& m, bool& negate)
+{
+    return n > 32 && column_classes(A, n, 32, B, m, negate);
 }
 
 int enqueue_range(DeviceCtx* c, const uint8_t* dA, int n, int m, uint64_t first, uint64_t last,
@@ -198,6 +203,8 @@ int enqueue_range(DeviceCtx* c, const uint8_t* dA, int n, int m, uint64_t first,
     return scratch_release(c->scratch_free, stream, capturing);
 }
 
+uint64_t full_range_last(int n) { return n >= 64 ? ~0ull : (1ull << n) - 1; }
+
 int valid_range(int n, uint64_t first, uint64_t last)
 {
     if (n < 1 || n > PF3_MAX_N || first > last) return PF3_EINVAL;
@@ -219,11 +226,15 @@ int host_range(const uint8_t* A, int n, uint64_t first, uint64_t last, uint64_t*
     DeviceCtx* c = device_ctx(&rc);
     if (!c) return rc;
     std::lock_guard<std::mutex> g(c->mu);
+    // a whole range of a narrow merged matrix: counted by column-sum vector
+    const bool by_class = merged && m <= c->class_max_cols && first == 0 && last == full_range_last(n);
     const size_t bytes = (size_t)n * m;
     std::memcpy(c->h_A, merged ? B.data() : A, bytes);
     cudaError_t e = cudaMemcpyAsync(c->d_A, c->h_A, bytes, cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) return cuda_rc(e);
-    if ((rc = enqueue_range(c, c->d_A, n, m, first, last, c->d_out, c->stream))) return rc;
+    rc = by_class ? enqueue_class_counts(c->d_A, n, m, c->d_out, c->stream)
+                  : enqueue_range(c, c->d_A, n, m, first, last, c->d_out, c->stream);
+    if (rc) return rc;
     e = cudaMemcpyAsync(c->h_out, c->d_out, sizeof(unsigned long long) * 3, cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess) return cuda_rc(e);
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_rc(e);
@@ -320,6 +331,51 @@ int pf3_column_merge(const uint8_t* A, int n, uint8_t* B, int* m, int* negate)
     *m = mm;
     *negate = neg ? 1 : 0;
     return 1;
+}
+
+int pf3_class_counts(const uint8_t* A, int n, uint64_t* plus, uint64_t* minus)
+{
+    if (!A || !plus || !minus || n < 1 || n > PF3_MAX_N) return PF3_EINVAL;
+    int rc = check_entries_host(A, n);
+    if (rc) return rc;
+    std::vector<uint8_t> B;
+    int m = n;
+    bool negate = false;
+    if (!column_classes(A, n, PF3_CLASS_MAX_COLS, B, m, negate)) return 0;  // nothing written
+    DeviceCtx* c = device_ctx(&rc);
+    if (!c) return rc;
+    std::lock_guard<std::mutex> g(c->mu);
+    std::memcpy(c->h_A, B.data(), B.size());
+    cudaError_t e = cudaMemcpyAsync(c->d_A, c->h_A, B.size(), cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_rc(e);
+    if ((rc = enqueue_class_counts(c->d_A, n, m, c->d_out, c->stream))) return rc;
+    e = cudaMemcpyAsync(c->h_out, c->d_out, sizeof(unsigned long long) * 3, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_rc(e);
+    if (c->h_out[2] == ~0ull) return PF3_EDOMAIN;
+    *plus = negate ? c->h_out[1] : c->h_out[0];
+    *minus = negate ? c->h_out[0] : c->h_out[1];
+    return 1;
+}
+
+int pf3_set_class_limit(int max_cols)
+{
+    if (max_cols < 0 || max_cols > PF3_CLASS_MAX_COLS) return PF3_EINVAL;
+    int rc;
+    DeviceCtx* c = device_ctx(&rc);
+    if (!c) return rc;
+    std::lock_guard<std::mutex> g(c->mu);
+    c->class_max_cols = max_cols;
+    return PF3_OK;
+}
+
+int pf3_get_class_limit(void)
+{
+    int rc;
+    DeviceCtx* c = device_ctx(&rc);
+    if (!c) return rc;
+    std::lock_guard<std::mutex> g(c->mu);
+    return c->class_max_cols;
 }
 
 int pf3_step_table(uint32_t* out)

@@ -6,6 +6,7 @@
 #include <mutex>
 #include <vector>
 
+#include "perm_f3.h"
 #include "pf3_batch.h"
 #include "pf3_internal.h"
 
@@ -56,6 +57,7 @@ struct DeviceCtx {
     int single_variant[2] = {0, 0};        // tuned single-kernel variant for W = 1 / W = 2
     int single_variant_short[2] = {0, 0};  // the same for launches of fewer than kShortLaunch indices
     int single_variant_merged = 0;         // long launches of a matrix with merged columns (one word)
+    int class_max_cols = PF3_CLASS_MAX_COLS;  // merged matrices this narrow are counted by class (0: never)
     int single_ctas[2][kMaxVariants] = {};  // resident CTAs per SM by W and variant (0 = not queried)
     int batch_ctas_cache[2][kMaxVariants] = {};
     int max_grid = 0;
@@ -91,6 +93,20 @@ int enqueue_range(DeviceCtx* c, const uint8_t* dA, int n, int m, uint64_t first,
 // the equal-column merge of the host-pointer calls (pf3_capi.cu): on true, B
 // (n x m, row-major), m and negate describe the matrix to walk instead of A
 bool merge_columns(const uint8_t* A, int n, std::vector<uint8_t>& B, int& m, bool& negate);
+// the same merge for any n, on true when the merged matrix has at most
+// max_cols columns
+bool column_classes(const uint8_t* A, int n, int max_cols, std::vector<uint8_t>& B, int& m, bool& negate);
+// Ryser counts of the whole range of the device matrix dB (n rows of m <=
+// PF3_CLASS_MAX_COLS columns) by column-sum vector (pf3_classes.cu), to d_out
+// as enqueue_range writes them; uses no scratch of the context
+int enqueue_class_counts(const uint8_t* dB, int n, int m, unsigned long long* d_out, cudaStream_t stream);
+size_t class_table_bytes(int m);
+// the serving kernel that counts, one CTA each, the jobs of a launch's slot
+// set-ups marked by items == 0 (args: const SlotInit* inits, int count, const
+// uint8_t* mats, int slot_bytes, unsigned long long* acc, unsigned* left,
+// uint8_t* results), with its block size and dynamic shared memory; nullptr
+// on a CUDA error
+const void* class_slots_fn(int* threads, size_t* smem);
 // Order work on `stream` that uses the buffers guarded by `ev` after the
 // previous user of those buffers (cudaStreamWaitEvent), and mark its end
 // (cudaEventRecord).  Inside a stream capture both do nothing: ordering the
@@ -98,6 +114,7 @@ bool merge_columns(const uint8_t* A, int n, std::vector<uint8_t>& B, int& m, boo
 int scratch_acquire(cudaEvent_t ev, cudaStream_t stream, bool* capturing);
 int scratch_release(cudaEvent_t ev, cudaStream_t stream, bool capturing);
 int check_entries_host(const uint8_t* A, int n);
+uint64_t full_range_last(int n);  // the last Gray index of an n-row walk
 int single_ctas(DeviceCtx* c, int W, int v);
 void load_tune_cache(DeviceCtx* c);
 int batch_ctas(DeviceCtx* c, int W, int v);

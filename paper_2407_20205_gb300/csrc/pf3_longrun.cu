@@ -111,8 +111,31 @@ int pf3_longrun(const uint8_t* A, int n, int chunk_log2, const char* checkpoint_
     std::vector<uint8_t> B;
     int m = n;
     bool negate = false;
-    const uint8_t* src = merge_columns(A, n, B, m, negate) ? B.data() : A;
+    const bool merged = merge_columns(A, n, B, m, negate);
+    const uint8_t* src = merged ? B.data() : A;
     const size_t bytes = (size_t)n * m;
+    if (merged && ck.cursor == 0 && !ck.done && !g_cancel.load()) {
+        // a fresh run of a narrow merged matrix: the whole range at once by
+        // column-sum vector (pf3_classes.cu), one short launch
+        std::lock_guard<std::mutex> g(c->mu);
+        if (m <= c->class_max_cols) {
+            std::memcpy(c->h_A, src, bytes);
+            cudaError_t e = cudaMemcpyAsync(c->d_A, c->h_A, bytes, cudaMemcpyHostToDevice, c->stream);
+            if (!(rc = cuda_rc(e))) rc = enqueue_class_counts(c->d_A, n, m, c->d_out, c->stream);
+            if (!rc) {
+                e = cudaMemcpyAsync(c->h_out, c->d_out, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                    c->stream);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+                rc = cuda_rc(e);
+            }
+            if (!rc) {
+                ck.plus = negate ? c->h_out[1] : c->h_out[0];
+                ck.minus = negate ? c->h_out[0] : c->h_out[1];
+                ck.done = 1;
+                if (checkpoint_path && !write_checkpoint(checkpoint_path, ck)) rc = PF3_EINVAL;
+            }
+        }
+    }
     while (!rc && !ck.done) {
         if (g_cancel.load()) {
             rc = PF3_ECANCELED;

@@ -56,6 +56,7 @@ struct Job {
     int n = 0;
     int m = 0;                // columns walked: n, or fewer when equal columns were merged
     bool negate = false;      // the merge's sign factor: the result is negated
+    bool by_class = false;    // counted by column-sum vector when admitted, not walked
     int state = kQueued;
     int slot = -1;
     int result = -1;
@@ -103,7 +104,7 @@ struct pf3_ctx {
     // its sizes in the instantiated graph and replays it (see build_graph).
     cudaGraph_t graph[2] = {nullptr, nullptr};
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    cudaGraphNode_t g_stage[2] = {}, g_inits[2] = {}, g_items[2] = {}, g_slot[2] = {};
+    cudaGraphNode_t g_stage[2] = {}, g_inits[2] = {}, g_items[2] = {}, g_slot[2] = {}, g_class[2] = {};
     cudaGraphNode_t g_batch[2][2] = {};  // [buffer][class]
     // host bookkeeping
     std::mutex mu;
@@ -214,6 +215,22 @@ int build_graph(pf3_ctx* x, int b)
     kp.kernelParams = sargs;
     if (e == cudaSuccess) e = cudaGraphAddKernelNode(&x->g_slot[b], g, &prev, 1, &kp);
     if (e == cudaSuccess) dep(x->g_slot[b]);
+    // the jobs counted by column-sum vector (pf3_classes.cu), one CTA each
+    int class_threads = 0;
+    size_t class_smem = 0;
+    const void* class_fn = class_slots_fn(&class_threads, &class_smem);
+    if (e == cudaSuccess && !class_fn) e = cudaErrorInvalidValue;
+    const uint8_t* mats = x->d_mats;
+    void* cargs[] = {(void*)&d_inits, (void*)&count, (void*)&mats, (void*)&slot_bytes,
+                     (void*)&x->d_acc, (void*)&x->d_left, (void*)&x->d_results};
+    cudaKernelNodeParams cp = {};
+    cp.func = (void*)class_fn;
+    cp.gridDim = dim3(1);
+    cp.blockDim = dim3((unsigned)class_threads);
+    cp.sharedMemBytes = (unsigned)class_smem;
+    cp.kernelParams = cargs;
+    if (e == cudaSuccess) e = cudaGraphAddKernelNode(&x->g_class[b], g, &prev, 1, &cp);
+    if (e == cudaSuccess) dep(x->g_class[b]);
     cudaMemsetParams mp = {};
     mp.dst = x->d_cursor + 2 * b;
     mp.value = 0;
@@ -262,6 +279,11 @@ int build_graph(pf3_ctx* x, int b)
 void plan_job_items(Job& j, const pf3_config& cfg, const int U_cls[2])
 {
     const int U = U_cls[j.m <= 32 ? 0 : 1];
+    if (j.by_class) {  // no work items
+        j.nb = 0;
+        j.items_total = 0;
+        return;
+    }
     if (j.n <= U) {
         j.nb = 0;
         j.items_total = 1;
@@ -362,7 +384,7 @@ bool launch_once(pf3_ctx* x)
     std::vector<WorkItem> cls_items[2];
     Launch L;
     L.buf = buf;
-    int n_inits = 0;
+    int n_inits = 0, n_class = 0;
     size_t stage_off = 0;
     {
         std::lock_guard<std::mutex> g(x->mu);
@@ -384,10 +406,15 @@ bool launch_once(pf3_ctx* x)
             inits[n_inits].slot = j.slot;
             inits[n_inits].n = j.n;
             inits[n_inits].cols = (unsigned)j.m;
-            inits[n_inits].items = (unsigned)j.items_total;
+            inits[n_inits].items = (unsigned)j.items_total;  // 0: counted by class in this launch
             ++n_inits;
             stage_off += nn;
-            x->active.push_back(tk);
+            if (j.by_class) {
+                ++n_class;
+                L.finishing.push_back(tk);
+            } else {
+                x->active.push_back(tk);
+            }
         }
         // choose items: small jobs first, then the others in arrival order
         select_items(x->jobs, x->active, x->cfg, x->U, cls_items, L.finishing);
@@ -425,6 +452,23 @@ bool launch_once(pf3_ctx* x)
         e = cudaGraphExecKernelNodeSetParams(ge, x->g_slot[buf], &kp);
     }
     if (e == cudaSuccess) e = cudaGraphNodeSetEnabled(ge, x->g_slot[buf], n_inits ? 1u : 0u);
+    if (e == cudaSuccess && n_class) {
+        const SlotInit* d_inits = (const SlotInit*)x->d_table[buf];
+        int count = n_inits, slot_bytes = kSlotBytes;
+        const uint8_t* mats = x->d_mats;
+        void* cargs[] = {(void*)&d_inits, (void*)&count, (void*)&mats, (void*)&slot_bytes,
+                         (void*)&x->d_acc, (void*)&x->d_left, (void*)&x->d_results};
+        int threads = 0;
+        size_t smem = 0;
+        cudaKernelNodeParams cp = {};
+        cp.func = (void*)class_slots_fn(&threads, &smem);
+        cp.gridDim = dim3((unsigned)n_inits);
+        cp.blockDim = dim3((unsigned)threads);
+        cp.sharedMemBytes = (unsigned)smem;
+        cp.kernelParams = cargs;
+        e = cp.func ? cudaGraphExecKernelNodeSetParams(ge, x->g_class[buf], &cp) : cudaErrorInvalidValue;
+    }
+    if (e == cudaSuccess) e = cudaGraphNodeSetEnabled(ge, x->g_class[buf], n_class ? 1u : 0u);
     const WorkItem* d_items = (const WorkItem*)((char*)x->d_table[buf] + inits_bytes);
     for (int cls = 1; cls >= 0 && e == cudaSuccess; --cls) {
         const size_t cnt = cls == 1 ? n1 : n0;
@@ -510,13 +554,15 @@ void pf3_config_default(pf3_config* cfg)
     cfg->max_admit = 1024;
     cfg->small_work_log2 = 33;
     cfg->launch_budget = 1ull << 33;
+    cfg->class_max_cols = PF3_CLASS_MAX_COLS;
 }
 
 static bool valid_config(const pf3_config& cfg)
 {
     return !(cfg.max_jobs < 1 || cfg.max_jobs > (1 << 20) || cfg.queue_depth < 1 || cfg.chunk_log2 < 13 ||
              cfg.chunk_log2 > 62 || cfg.launch_items < 1 || cfg.max_admit < 1 || cfg.launch_budget < 1 ||
-             cfg.small_work_log2 < 0 || cfg.small_work_log2 > 64);
+             cfg.small_work_log2 < 0 || cfg.small_work_log2 > 64 || cfg.class_max_cols < 0 ||
+             cfg.class_max_cols > PF3_CLASS_MAX_COLS);
 }
 
 int pf3_serve_plan(const int32_t* ns, const int32_t* ms, int64_t count, const pf3_config* cfg_in, const int* U,
@@ -537,8 +583,9 @@ int pf3_serve_plan(const int32_t* ns, const int32_t* ms, int64_t count, const pf
         j.n = n;
         j.m = m;
         j.slot = (int)k;
+        j.by_class = m < n && n > 32 && m <= cfg.class_max_cols;
         plan_job_items(j, cfg, U);
-        active.push_back(k);
+        if (!j.by_class) active.push_back(k);
     }
     std::vector<pf3_serve_item> out;
     for (int l = 0; l < launches && !active.empty(); ++l) {
@@ -713,6 +760,8 @@ int64_t perm_f3_submit(pf3_ctx* x, const uint8_t* A, int n)
     std::vector<uint8_t> B;
     if (merge_columns(A, n, B, j.m, j.negate)) {
         j.A.swap(B);
+        // few columns left: counted by column-sum vector (pf3_classes.cu)
+        j.by_class = j.m <= x->cfg.class_max_cols;
     } else {
         j.m = n;
         j.A.assign(A, A + (size_t)n * n);

@@ -193,17 +193,22 @@ def test_dense_terms_closed_form(pf3, n):
     send every warp into the dense walk: the exact counts must equal the
     closed form, for J_n and for D1 J D2 with random signs -- through the
     device-pointer path (A as it is: two plane words for n > 32) and the
-    host-pointer one (for n > 32 the columns merge into one or two)."""
+    host-pointer one (for n > 32 the columns merge into one or two, which are
+    counted by column-sum vector; with the class limit at 0 the merged matrix
+    is walked)."""
     J = np.ones((n, n), np.uint8)
-    want = rank_one_counts([1] * n, [1] * n)
-    assert pf3.perm_f3_counts(J) == want
-    assert _device_counts(pf3, J) == want
     A, d, e = _rank_one(7000 + n, n)
-    want = rank_one_counts(list(d), list(e))
-    assert pf3.perm_f3_counts(A) == want
-    assert _device_counts(pf3, A) == want
-    if n > 32:
-        assert pf3.column_merge(A) is not None
+    keep = pf3.get_class_limit()
+    for M, want in ((J, rank_one_counts([1] * n, [1] * n)), (A, rank_one_counts(list(d), list(e)))):
+        assert pf3.perm_f3_counts(M) == want
+        assert _device_counts(pf3, M) == want
+        if n > 32:
+            assert pf3.column_merge(M) is not None
+            try:
+                pf3.set_class_limit(0)
+                assert pf3.perm_f3_counts(M) == want
+            finally:
+                pf3.set_class_limit(keep)
 
 
 def test_dense_terms_batch_and_ranges(pf3, oracle):

@@ -95,9 +95,21 @@ def test_all_small_is_least_remaining_first(pf3):
 
 
 def test_merged_columns_take_the_one_word_class(pf3):
-    items = plan(pf3, [40, 40, 36], ms=[2, 40, 33])
+    items = plan(pf3, [40, 40, 36], ms=[12, 40, 33])
     cls = {it["request"]: it["cls"] for it in items}
     assert cls == {0: 0, 1: 1, 2: 1}
+
+
+def test_narrow_merged_requests_are_counted_by_class(pf3):
+    """A request whose merged matrix (n > 32) has at most class_max_cols
+    columns gets no work items: it is counted by column-sum vector in the
+    launch that admits it.  With class_max_cols = 0 it is walked."""
+    ns, ms = [40, 36, 40, 20], [2, 8, 9, 20]
+    items = plan(pf3, ns, ms=ms)
+    assert {it["request"] for it in items} == {2, 3}
+    items = plan(pf3, ns, ms=ms, class_max_cols=0)
+    assert {it["request"] for it in items} == {0, 1, 2, 3}
+    assert {it["cls"] for it in items if it["request"] in (0, 1)} == {0}
 
 
 def test_bad_arguments(pf3):
@@ -106,6 +118,9 @@ def test_bad_arguments(pf3):
             pf3.serve_plan(ns, ms, launches=1, U=u)
     with pytest.raises(pf3.PF3Error):
         pf3.serve_plan([20], launches=1, U=U, chunk_log2=5)
+    for bad in (-1, pf3.CLASS_MAX_COLS + 1):
+        with pytest.raises(pf3.PF3Error):
+            pf3.serve_plan([20], launches=1, U=U, class_max_cols=bad)
 
 
 def test_too_small_a_buffer_writes_nothing(pf3):
