@@ -67,3 +67,23 @@ def test_merged_terms_match_the_oracle(pf3, oracle, n, pool):
         assert ((got[1], got[0]) if neg else got) == want
         nonzero += sum(want)
     assert nonzero > 100
+
+
+def test_class_counts_refusals_touch_no_device(pf3):
+    """pf3_class_counts merges on the host first: a matrix whose columns merge
+    into more than 8 is left to the walk (None) and a bad entry or size is an
+    error, all before any device is needed."""
+    assert pf3.class_counts(inputs.uniform_matrix(inputs.SEED_N20, 20)) is None
+    # 9 distinct columns (no two equal up to sign), n = 9
+    A = np.zeros((9, 9), np.uint8)
+    for j in range(9):
+        A[j, j] = 1
+    assert pf3.class_counts(A) is None
+    bad = np.ones((5, 5), np.uint8)
+    bad[1, 1] = 7
+    with pytest.raises(pf3.PF3Error) as ei:
+        pf3.class_counts(bad)
+    assert ei.value.code == pf3.PF3_EDOMAIN
+    assert pf3._lib_class_counts(None, 4, None, None) == pf3.PF3_EINVAL
+    with pytest.raises(pf3.PF3Error):
+        pf3.class_counts(np.zeros((65, 65), np.uint8))
