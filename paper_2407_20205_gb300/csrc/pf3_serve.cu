@@ -12,9 +12,11 @@
 // other jobs in arrival order.  Small jobs finish in the next launch, and
 // since they carry a small share of the work the large ones are served much
 // as first-come first-served would serve them, never behind a later large
-// job.  Up to two launches are in flight; new requests are
-// admitted into free slots between launches, so work that arrives while
-// other jobs run overlaps with them on the GPU.  Each launch's sequence of
+// job.  A job whose equal columns merge into at most cfg.class_max_cols
+// columns gets no work items: it is counted by column-sum vector
+// (pf3_classes.cu) in the launch that admits it.  Up to two launches are in
+// flight; new requests are admitted into free slots between launches, so
+// work that arrives while other jobs run overlaps with them on the GPU.  Each launch's sequence of
 // copies, kernels and event operations is one CUDA graph per buffer, replayed
 // with that launch's sizes.  Nothing on the device waits on the host:
 // completion is observed with CUDA events, and the host polls them with short
@@ -178,9 +180,11 @@ bool harvest(pf3_ctx* x, bool block)
 
 // The launch sequence of buffer b as a graph, one chain of nodes: copies of
 // the staged matrices, the slot set-ups and the work items to the device; the
-// slot set-up kernel; the reset of the item cursors; the batch kernel for
-// n > 32 and the one for n <= 32; then, after the other buffer's previous
-// kernels (event wait), the copy of every slot's result byte to the host.
+// slot set-up kernel; the count by column-sum vector of the admitted jobs
+// whose merged matrix is narrow; the reset of the item cursors; the batch
+// kernel for n > 32 and the one for n <= 32; then, after the other buffer's
+// previous kernels (event wait), the copy of every slot's result byte to the
+// host.
 // Sizes, grids and item counts change from launch to launch: launch_once
 // sets them in the instantiated graph and disables the nodes a launch does
 // not need (no admissions, no items of a class).
