@@ -228,3 +228,39 @@ def test_no_mod3_arithmetic_in_python_package():
                     if (f, None) not in allowed and (f, owner) not in allowed:
                         offenders.append(f"{f}:{node.lineno}")
     assert not offenders, sorted(set(offenders))
+
+
+def test_binding_constants_match_the_header():
+    """Every #define of the header that the binding mirrors has the same value
+    (evaluated by a C compiler, so expressions such as (1 << 24) count)."""
+    import re
+    from paper_2407_20205_gb300 import binding
+    text = open(os.path.join(ROOT, "include", "perm_f3.h")).read()
+    names = [m for m in re.findall(r"^#define (PF3_\w+) ", text, re.M)]
+    pairs = {}
+    for name in names:
+        short = name[len("PF3_"):]
+        for cand in (name, short):
+            if hasattr(binding, cand):
+                pairs[name] = getattr(binding, cand)
+                break
+    # the ones a caller of the binding relies on must be there
+    for must in ("PF3_EINVAL", "PF3_ETOOBIG", "PF3_MAX_N", "PF3_CLASS_MAX_COLS", "PF3_NOALLOC_MAX_CTAS",
+                 "PF3_LONGRUN_MAX_CHUNK_LOG2", "PF3_VEC_MAX_N", "PF3_TINY_MAX_N"):
+        assert must in pairs, must
+    import subprocess
+    import tempfile
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "defs.c")
+        with open(src, "w") as f:
+            f.write('#include <stdio.h>\n#include "perm_f3.h"\nint main(void) {\n')
+            for name in pairs:
+                f.write(f'    printf("{name} %lld\\n", (long long)({name}));\n')
+            f.write("    return 0;\n}\n")
+        exe = os.path.join(d, "defs")
+        subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), src, "-o", exe], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
+    got = dict((k, int(v)) for k, v in (line.split() for line in out.splitlines()))
+    for name, val in pairs.items():
+        if isinstance(val, int):  # tuples such as SPLIT_CANDIDATES list values, not a count
+            assert got[name] == val, (name, got[name], val)
