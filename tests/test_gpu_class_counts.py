@@ -76,7 +76,7 @@ def test_wide_matrix_is_not_counted(pf3):
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 7, 20, 33, 39, 40, 47, 63, 64])
-def test_rank_one_closed_form(pf3, n):
+def test_rank_one_closed_form_by_class(pf3, n):
     """J_n and D1 J D2 (random signs): one or two merged columns; the counts
     have a closed form (the column sums over S are e_j times a signed count
     of S), also at n = 64 where they approach 2^63 -- through
